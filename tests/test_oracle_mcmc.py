@@ -1,0 +1,179 @@
+"""Pins of the oracle's sampler (no GPU): closed-form posteriors of a
+linear-Gaussian toy, prior-only targets, delayed-acceptance exactness with a
+deliberately poor surrogate, and the effective sample size of an AR(1) chain
+whose integrated autocorrelation time is known in closed form."""
+import numpy as np
+import pytest
+
+from oracle import mcmc
+
+
+def _ess_pooled(samples):
+    """Sum over chains of the per-chain ESS (for MCSE bounds in these tests)."""
+    S, P, C = samples.shape
+    return np.array([sum(mcmc.ess_plain(samples[:, p, c]) for c in range(C)) for p in range(P)])
+
+
+def _toy_model(lo=-10.0, hi=10.0, step=(0.3, 0.3)):
+    return mcmc.Model(param_map=[0, 1], fixed=np.zeros(5), prior_kind=["uniform"] * 2,
+                      prior_p0=np.array([lo, lo]), prior_p1=np.array([hi, hi]),
+                      step_space=["linear"] * 2, step=np.array(step))
+
+
+A_TOY = np.array([[1.0, 0.5], [0.2, 1.5], [0.7, -0.4]])
+Y_TOY = np.array([1.0, 2.0, 0.3])
+SIG_TOY = 0.5
+
+
+def _toy_phi(theta_full):
+    th = theta_full[:, :2]
+    r = Y_TOY[None, :] - th @ A_TOY.T
+    return (r * r).sum(1) / (2 * SIG_TOY**2), np.zeros(th.shape[0], np.uint32)
+
+
+def _toy_posterior():
+    prec = A_TOY.T @ A_TOY / SIG_TOY**2
+    cov = np.linalg.inv(prec)
+    mean = cov @ (A_TOY.T @ Y_TOY) / SIG_TOY**2
+    return mean, cov
+
+
+def _check_gaussian(samples, mean, cov, burn=200):
+    kept = samples[burn:]
+    ess = _ess_pooled(kept)
+    pooled = kept.transpose(1, 0, 2).reshape(2, -1)
+    sd = np.sqrt(np.diag(cov))
+    mcse = sd / np.sqrt(ess)
+    assert np.all(np.abs(pooled.mean(1) - mean) < 3.5 * mcse), (pooled.mean(1), mean, mcse)
+    # variance: MCSE of a Gaussian variance estimate ~ var * sqrt(2 / ess)
+    var = pooled.var(1, ddof=1)
+    assert np.all(np.abs(var - sd**2) < 3.5 * sd**2 * np.sqrt(2 / ess)), (var, sd**2)
+
+
+def test_linear_gaussian_posterior():
+    """G(theta) = A theta with Gaussian noise and a flat (very wide uniform)
+    prior: the posterior is N((A'A)^-1 A'y, sigma^2 (A'A)^-1)."""
+    mean, cov = _toy_posterior()
+    m = _toy_model()
+    ch = mcmc.Chains(m, np.tile(mean, (32, 1)) + 0.1, seed=3, phi_fn=_toy_phi)
+    samples = ch.run(1500)
+    _check_gaussian(samples, mean, cov)
+    assert 0.2 < ch.n_acc / ch.n_prop < 0.9
+
+
+def test_delayed_acceptance_is_exact_with_poor_surrogate():
+    """Christen-Fox exactness: a surrogate that is wrong (scaled, shifted and
+    tilted) still leaves the posterior unchanged."""
+    mean, cov = _toy_posterior()
+    m = _toy_model()
+
+    def bad_surrogate(theta):
+        phi, _ = _toy_phi(m.full_theta(theta))
+        return 0.6 * phi + 3.0 * theta[:, 0] - 7.0
+
+    ch = mcmc.Chains(m, np.tile(mean, (32, 1)) - 0.1, seed=5, phi_fn=_toy_phi,
+                     surrogate=bad_surrogate)
+    samples = ch.run(1500)
+    _check_gaussian(samples, mean, cov)
+    assert ch.n_solves == ch.n_pass1 < ch.n_prop
+
+
+def test_uniform_prior_flat_likelihood():
+    """Phi = 0 with a uniform prior on [0, 1] x [0, 2]: samples are uniform
+    (mean at the centre, variance (hi - lo)^2 / 12)."""
+    m = mcmc.Model(param_map=[0, 1], fixed=np.zeros(5), prior_kind=["uniform"] * 2,
+                   prior_p0=np.array([0.0, 0.0]), prior_p1=np.array([1.0, 2.0]),
+                   step_space=["linear"] * 2, step=np.array([0.3, 0.6]))
+    flat = lambda th: (np.zeros(th.shape[0]), np.zeros(th.shape[0], np.uint32))
+    ch = mcmc.Chains(m, np.tile([0.5, 1.0], (32, 1)), seed=9, phi_fn=flat)
+    s = ch.run(1500)[100:]
+    ess = _ess_pooled(s)
+    pooled = s.transpose(1, 0, 2).reshape(2, -1)
+    sd = np.array([1.0, 2.0]) / np.sqrt(12)
+    assert np.all(np.abs(pooled.mean(1) - [0.5, 1.0]) < 3.5 * sd / np.sqrt(ess))
+    assert np.all((pooled >= [[0.0], [0.0]]) & (pooled <= [[1.0], [2.0]]))
+    assert np.allclose(pooled.var(1), sd**2, rtol=0.1)
+
+
+def test_lognormal_prior_in_log_space():
+    """Phi = 0, log-normal prior (median m, sigma s), random walk in log theta:
+    log theta ~ N(log m, s^2)."""
+    med, sig = np.array([10.0, 200.0]), np.array([0.5, 0.5])
+    m = mcmc.Model(param_map=[2, 3], fixed=np.array([0.1, 0.9, 0, 0, 0]),
+                   prior_kind=["lognormal"] * 2, prior_p0=med, prior_p1=sig,
+                   step_space=["log"] * 2, step=np.array([0.6, 0.6]))
+    flat = lambda th: (np.zeros(th.shape[0]), np.zeros(th.shape[0], np.uint32))
+    ch = mcmc.Chains(m, np.tile(med, (32, 1)), seed=11, phi_fn=flat)
+    s = np.log(ch.run(1500)[100:])
+    ess = _ess_pooled(s)
+    pooled = s.transpose(1, 0, 2).reshape(2, -1)
+    assert np.all(np.abs(pooled.mean(1) - np.log(med)) < 3.5 * sig / np.sqrt(ess))
+    assert np.allclose(pooled.std(1), sig, rtol=0.08)
+
+
+def test_lognormal_prior_with_linear_steps():
+    """The same log-normal target sampled with steps in theta itself (the
+    prior density then carries its 1/theta factor): log theta ~ N(log m, s^2)."""
+    med, sig = np.array([2.0]), np.array([0.3])
+    m = mcmc.Model(param_map=[2], fixed=np.array([0.1, 0.9, 0, 200, 0]),
+                   prior_kind=["lognormal"], prior_p0=med, prior_p1=sig,
+                   step_space=["linear"], step=np.array([1.0]))
+    flat = lambda th: (np.zeros(th.shape[0]), np.zeros(th.shape[0], np.uint32))
+    ch = mcmc.Chains(m, np.tile(med, (32, 1)), seed=12, phi_fn=flat)
+    s = np.log(ch.run(2000)[100:])
+    ess = _ess_pooled(s)
+    pooled = s.reshape(-1)
+    assert abs(pooled.mean() - np.log(2.0)) < 3.5 * 0.3 / np.sqrt(ess[0])
+    assert pooled.std() == pytest.approx(0.3, rel=0.08)
+
+
+def test_rejects_outside_support_and_nonfinite():
+    m = _toy_model(lo=0.0, hi=1.0, step=(5.0, 5.0))
+    calls = []
+
+    def phi_fn(th):
+        calls.append(th.copy())
+        return np.zeros(th.shape[0]), np.zeros(th.shape[0], np.uint32)
+
+    ch = mcmc.Chains(m, np.tile([0.5, 0.5], (64, 1)), seed=1, phi_fn=phi_fn)
+    s = ch.run(20)
+    evaluated = np.concatenate(calls[1:])[:, :2]
+    assert np.all((evaluated >= 0) & (evaluated <= 1))  # no solve outside support
+    assert np.all((s >= 0) & (s <= 1))
+
+    def nan_fn(th):
+        return np.full(th.shape[0], np.nan), np.full(th.shape[0], 2, np.uint32)
+
+    m2 = _toy_model()
+    ch2 = mcmc.Chains(m2, np.tile([0.5, 0.5], (8, 1)), seed=1, phi_fn=_toy_phi)
+    ch2.phi_fn = nan_fn
+    before = ch2.theta.copy()
+    ch2.run(10)
+    assert np.array_equal(ch2.theta, before)
+
+
+@pytest.mark.parametrize("phi", [0.0, 0.5, 0.9])
+def test_ess_of_ar1(phi):
+    """AR(1) x_t = phi x_{t-1} + e_t has integrated autocorrelation time
+    (1 + phi) / (1 - phi), so ESS = n (1 - phi) / (1 + phi)."""
+    rng = np.random.default_rng(int(phi * 10))
+    n, reps = 20000, 8
+    vals = []
+    for _ in range(reps):
+        e = rng.standard_normal(n)
+        x = np.empty(n)
+        x[0] = e[0] / np.sqrt(1 - phi**2)
+        for t in range(1, n):
+            x[t] = phi * x[t - 1] + e[t]
+        vals.append(mcmc.ess_plain(x))
+    expect = n * (1 - phi) / (1 + phi)
+    assert np.mean(vals) == pytest.approx(expect, rel=0.1)
+
+
+def test_summarize_credible_interval():
+    rng = np.random.default_rng(0)
+    s = rng.standard_normal((4000, 1, 8))
+    out = mcmc.summarize(s, burn_frac=0.25)
+    assert out["q025"][0] == pytest.approx(-1.96, abs=0.05)
+    assert out["q975"][0] == pytest.approx(1.96, abs=0.05)
+    assert abs(out["mean"][0]) < 0.03
