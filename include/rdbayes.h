@@ -1,0 +1,193 @@
+/*
+ * rdbayes.h -- C ABI of the GB300 library for Bayesian identification of the
+ * parameters of the Schnakenberg reaction-diffusion system (arXiv:1605.04718).
+ *
+ * The method (Sec. 2): data y = G(p) + eta with Gaussian noise (eq.
+ * (meas_model)); log-likelihood Phi(p; y) = -log rho(y - G(p)) (eq. (logl));
+ * posterior mu^y(p) proportional to exp(-Phi(p; y)) mu_0(p) (eq. (bayes));
+ * sampled by Metropolis-Hastings (Algorithm 1) over many independent chains,
+ * with burn-in and pooling as in Sec. 2.1.  G solves the system of eq.
+ * (schnakenberg) with the kinetics of eq. (reactions),
+ *     u_t + m r u = rho^-2 Lap u + gamma (a - u + u^2 v),
+ *     v_t + m r v = d rho^-2 Lap v + gamma (b - u^2 v),
+ * on the unit interval or square with Neumann boundaries, rho(t) = exp(r t)
+ * (rho = 1 on a fixed domain), by the finite-difference IMEX Euler step of
+ * Sec. 3.1.1 with the reaction explicit and diffusion plus dilution implicit.
+ *
+ * Conventions for every call:
+ *  - Returns an rd_status; never aborts.  rd_last_error() gives a message
+ *    for the calling thread.
+ *  - Parameter vectors are in natural units, in the order (a, b, d, gamma, r)
+ *    mapped through rd_problem_desc.param_map.
+ *  - "device" pointers are CUDA device addresses on the problem's device;
+ *    "host" pointers are ordinary host memory.  The caller owns every pointer
+ *    it passes; the library copies or consumes inputs in stream order and
+ *    never keeps a caller pointer after the call's work has completed.
+ *  - All GPU work is enqueued on the problem's CUDA stream (cudaStream_t passed
+ *    as void*; NULL = the legacy default stream).  Calls marked "async" return
+ *    before the work is done; rd_sync waits for it.
+ *  - Per-proposal failures are status bits with Phi = +inf, not call errors
+ *    (the paper's requirement that the log-likelihood be robust, Sec. 2).
+ *  - There is no CPU fallback: without a CUDA device every call that needs one
+ *    returns RD_ECUDA.
+ */
+#ifndef RDBAYES_H
+#define RDBAYES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rd_problem rd_problem;
+typedef struct rd_chains rd_chains;
+typedef struct rd_surrogate rd_surrogate;
+
+typedef enum {
+  RD_OK = 0,
+  RD_EINVAL = 1,   /* invalid argument (message in rd_last_error) */
+  RD_ENOMEM = 2,   /* device or host allocation failed */
+  RD_ECUDA = 3,    /* a CUDA runtime call failed, or no device */
+  RD_ESTATE = 4,   /* call out of order (e.g. no observations set) */
+  RD_ETIMEOUT = 5  /* a bounded device wait gave up */
+} rd_status;
+
+/* Per-proposal status bits. */
+enum {
+  RD_P_OK = 0,
+  RD_P_OUT_OF_SUPPORT = 1, /* prior density zero: rejected without a solve */
+  RD_P_NONFINITE = 2,      /* non-finite or |w| > w_max at an observation */
+  RD_P_NOT_CONVERGED = 4   /* iterative solve hit its iteration cap */
+};
+
+/* Implicit-diffusion solver of the IMEX step. */
+enum {
+  RD_SOLVER_AUTO = 0,      /* autotuned per grid size (2-D), Thomas (1-D) */
+  RD_SOLVER_THOMAS = 1,    /* 1-D tridiagonal (FP64) */
+  RD_SOLVER_DCT_SIMT = 2,  /* 2-D eigenbasis solve, FP32 CUDA-core GEMMs */
+  RD_SOLVER_DCT_TC = 3     /* 2-D eigenbasis solve, split-FP16 tcgen05 GEMMs */
+};
+
+enum { RD_PRIOR_UNIFORM = 0, RD_PRIOR_LOGNORMAL = 1 };
+enum { RD_STEP_LINEAR = 0, RD_STEP_LOG = 1 };
+enum { RD_PREC_F64 = 0, RD_PREC_F32 = 1 };
+
+#define RD_MAX_SIZES 4
+#define RD_MAX_OBS 8
+#define RD_NPARAM 5
+
+/*
+ * Problem description.  Grid: cell-centred, x_i = (i + 1/2)/N, h = 1/N, in
+ * each dimension.  One problem may hold up to RD_MAX_SIZES grid sizes (each
+ * with its own initial state and observations) whose proposals are batched
+ * together in one launch.
+ */
+typedef struct {
+  int dim;                    /* 1 or 2 */
+  int n_sizes;                /* 1..RD_MAX_SIZES */
+  int nx[RD_MAX_SIZES];       /* grid points per side; 2-D: multiple of 16, 16..128;
+                                 1-D: 2..256 */
+  double tau;                 /* time step */
+  int n_steps;                /* steps to the final time T = n_steps * tau */
+  int precision;              /* RD_PREC_F64 (1-D) or RD_PREC_F32 (2-D fields) */
+  int solver;                 /* RD_SOLVER_* */
+  int growth;                 /* 0: rho = 1 (r ignored); 1: rho = exp(r t), m = dim */
+  int n_params;               /* number of inferred parameters P, 1..5 */
+  int param_map[RD_NPARAM];   /* index in (a, b, d, gamma, r) of inferred parameter j */
+  double fixed[RD_NPARAM];    /* values of the parameters that are not inferred */
+  int prior_kind[RD_NPARAM];  /* per inferred parameter: RD_PRIOR_* */
+  double prior_p0[RD_NPARAM]; /* uniform: lower bound; log-normal: median */
+  double prior_p1[RD_NPARAM]; /* uniform: upper bound; log-normal: sigma of log */
+  int step_space[RD_NPARAM];  /* per inferred parameter: RD_STEP_* */
+  double w_max;               /* divergence bound (<= 0: default 100) */
+} rd_problem_desc;
+
+/* Creates a problem on the current CUDA device and stream `cuda_stream`.
+ * Allocates the library's device workspace.  EINVAL on an invalid desc. */
+rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
+                            rd_problem** out);
+rd_status rd_problem_destroy(rd_problem* p);
+rd_status rd_set_stream(rd_problem* p, void* cuda_stream);
+
+/* Initial state u0, v0 of grid size `size_idx` (host, N^dim values each,
+ * row-major with the first index along y).  The same fixed, known initial
+ * state is used for every proposal (Sec. 3.1.2).  Copied; stream-ordered. */
+rd_status rd_set_initial_state(rd_problem* p, int size_idx, const double* u0,
+                               const double* v0);
+
+/* Observations of size `size_idx`: n_times (1..RD_MAX_OBS) step indices
+ * obs_steps (increasing, in 1..n_steps), observed fields field_mask (1 = u,
+ * 2 = v, 3 = both), data y (host, [n_times][observed fields][N^dim]) and
+ * noise standard deviation sigma.  Phi = sum (y - w)^2 / (2 sigma^2) over all
+ * observed values (eq. (logl) with Gaussian noise).  Copied; stream-ordered. */
+rd_status rd_set_observations(rd_problem* p, int size_idx, int n_times,
+                              const int* obs_steps, int field_mask,
+                              const double* y, double sigma);
+
+/* Forward solves + log-likelihoods for B proposals (async).
+ * theta:    device, [B][n_params] inferred parameters (natural units)
+ * size_idx: device, [B] grid-size index of each proposal, or NULL (all 0)
+ * loglik:   device, [B] Phi (+inf when status != 0)
+ * status:   device, [B] RD_P_* bits
+ * fields:   device or NULL, [B][2][maxN^dim] final u, v (float for F32
+ *           problems, double for F64), each proposal at stride 2*maxN^dim
+ *           with its own N^dim values first. */
+rd_status rd_evaluate_batch(rd_problem* p, int B, const double* theta,
+                            const int* size_idx, double* loglik,
+                            uint32_t* status, void* fields);
+
+/* As rd_evaluate_batch with HOST theta/size_idx/loglik/status: copies in,
+ * solves, copies out, and returns when the results are in host memory. */
+rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
+                                 const int* size_idx, double* loglik,
+                                 uint32_t* status);
+
+/* Chains: n_chains independent random-walk Metropolis chains advanced in
+ * lock-step, one proposal per chain per step (Algorithm 1).
+ * theta0:   host [C][n_params] starting points
+ * seed:     Philox key; chain c at its step s draws from counters (c, s, 0|1, 0)
+ * step:     host [n_params] random-walk standard deviations in step space
+ * size_idx: host [C] grid size of each chain, or NULL (all 0)
+ * capacity: samples kept on the device before rd_chains_read_samples must be
+ *           called (each sample = [n_params][C] doubles). */
+rd_status rd_chains_create(rd_problem* p, int n_chains, const double* theta0,
+                           uint64_t seed, const double* step,
+                           const int* size_idx, int capacity,
+                           rd_chains** out);
+rd_status rd_chains_destroy(rd_chains* c);
+
+/* Advances every chain by n_steps (async; graph-replayed per step).
+ * ESTATE if the sample buffer would overflow. */
+rd_status rd_chains_run(rd_chains* c, int n_steps);
+
+/* Copies the samples accumulated since the last read into out (host,
+ * [n][n_params][C]; n <= cap_steps), sets *n_written, and fills
+ * counters[4] (if non-NULL) with the totals since creation: proposals,
+ * stage-1 survivors, accepted, exact solves.  Synchronises the stream. */
+rd_status rd_chains_read_samples(rd_chains* c, double* out, size_t cap_steps,
+                                 size_t* n_written, double* counters);
+
+/* Current state: theta (host [C][n_params]), phi (host [C]); either may be
+ * NULL.  Synchronises the stream. */
+rd_status rd_chains_get_state(rd_chains* c, double* theta, double* phi);
+
+/* Checkpoint of the full chain state (theta, Phi, surrogate Phi~, log prior,
+ * step counter, counters) into host memory; *n = bytes needed.  With
+ * buf == NULL only *n is set.  Restoring it into chains created with the same
+ * problem, C and seed continues the chains bit-identically. */
+rd_status rd_chains_checkpoint(rd_chains* c, void* buf, size_t cap, size_t* n);
+rd_status rd_chains_restore(rd_chains* c, const void* buf, size_t n);
+
+/* Blocks until all work enqueued on the problem's stream has finished. */
+rd_status rd_sync(rd_problem* p);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* rd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDBAYES_H */

@@ -1,0 +1,628 @@
+// rd_api.cu -- the extern "C" entry points declared in include/rdbayes.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "rd_common.cuh"
+#include "rd_internal.h"
+
+namespace rd {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+#define RD_CUDA(call)                                                      \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      rd::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
+      return RD_ECUDA;                                                     \
+    }                                                                      \
+  } while (0)
+
+#define RD_CHECK(cond, code, msg) \
+  do {                            \
+    if (!(cond)) {                \
+      rd::set_error(msg);         \
+      return code;                \
+    }                             \
+  } while (0)
+
+WorkQueue make_queue(const rd_problem* p) {
+  WorkQueue q;
+  q.items = p->ws.queue_items;
+  q.capacity = p->ws.capacity;
+  q.counts = p->ws.queue_counters;
+  q.pops = p->ws.queue_counters + kMaxSizes;
+  q.n_sizes = p->desc.n_sizes;
+  std::vector<int> order(p->desc.n_sizes);
+  for (int s = 0; s < p->desc.n_sizes; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return p->desc.nx[x] > p->desc.nx[y]; });
+  for (int k = 0; k < kMaxSizes; ++k) q.order[k] = k < (int)order.size() ? order[k] : 0;
+  return q;
+}
+
+cudaError_t launch_solve_on(rd_problem* p, const double* theta, double* phi,
+                            uint32_t* status, void* fields, cudaStream_t st) {
+  const int grid = grid_solve_simt(p->desc.dim, p->dev.max_n, p->n_sm);
+  return launch_solve_simt(p->dev, make_queue(p), theta, phi, status, fields,
+                           grid, st);
+}
+
+cudaError_t launch_solve(rd_problem* p, const double* theta, double* phi,
+                         uint32_t* status, void* fields) {
+  return launch_solve_on(p, theta, phi, status, fields, p->stream);
+}
+
+static rd_status ensure_capacity(rd_problem* p, int need) {
+  if (need <= p->ws.capacity) return RD_OK;
+  int cap = std::max(need, std::max(1024, 2 * p->ws.capacity));
+  RD_CUDA(cudaStreamSynchronize(p->stream));
+  if (p->ws.queue_items) RD_CUDA(cudaFree(p->ws.queue_items));
+  p->ws.queue_items = nullptr;
+  RD_CUDA(cudaMalloc(&p->ws.queue_items, sizeof(int) * (size_t)cap * p->desc.n_sizes));
+  p->ws.capacity = cap;
+  p->generation++;
+  return RD_OK;
+}
+
+static rd_status validate_desc(const rd_problem_desc* d) {
+  RD_CHECK(d, RD_EINVAL, "desc is NULL");
+  RD_CHECK(d->dim == 1 || d->dim == 2, RD_EINVAL, "dim must be 1 or 2");
+  RD_CHECK(d->n_sizes >= 1 && d->n_sizes <= RD_MAX_SIZES, RD_EINVAL,
+           "n_sizes must be in 1..4");
+  for (int s = 0; s < d->n_sizes; ++s) {
+    const int n = d->nx[s];
+    if (d->dim == 1) {
+      RD_CHECK(n >= 2 && n <= 256, RD_EINVAL, "1-D grid size must be in 2..256");
+    } else {
+      RD_CHECK(n >= 16 && n <= 128 && n % 16 == 0, RD_EINVAL,
+               "2-D grid size must be a multiple of 16 in 16..128");
+    }
+  }
+  RD_CHECK(d->tau > 0 && isfinite(d->tau), RD_EINVAL, "tau must be positive");
+  RD_CHECK(d->n_steps >= 1, RD_EINVAL, "n_steps must be >= 1");
+  RD_CHECK((d->dim == 1 && d->precision == RD_PREC_F64) ||
+               (d->dim == 2 && d->precision == RD_PREC_F32),
+           RD_EINVAL, "precision must be F64 for 1-D and F32 for 2-D problems");
+  RD_CHECK(d->solver == RD_SOLVER_AUTO || (d->dim == 1 && d->solver == RD_SOLVER_THOMAS) ||
+               (d->dim == 2 && (d->solver == RD_SOLVER_DCT_SIMT || d->solver == RD_SOLVER_DCT_TC)),
+           RD_EINVAL, "solver not available for this dimension");
+  RD_CHECK(d->n_params >= 1 && d->n_params <= RD_NPARAM, RD_EINVAL,
+           "n_params must be in 1..5");
+  for (int j = 0; j < d->n_params; ++j) {
+    RD_CHECK(d->param_map[j] >= 0 && d->param_map[j] < RD_NPARAM, RD_EINVAL,
+             "param_map entry out of range");
+    for (int k = 0; k < j; ++k)
+      RD_CHECK(d->param_map[k] != d->param_map[j], RD_EINVAL, "param_map repeats a parameter");
+    RD_CHECK(d->prior_kind[j] == RD_PRIOR_UNIFORM || d->prior_kind[j] == RD_PRIOR_LOGNORMAL,
+             RD_EINVAL, "unknown prior kind");
+    if (d->prior_kind[j] == RD_PRIOR_UNIFORM)
+      RD_CHECK(d->prior_p0[j] <= d->prior_p1[j], RD_EINVAL, "uniform prior needs lo <= hi");
+    else
+      RD_CHECK(d->prior_p0[j] > 0 && d->prior_p1[j] > 0, RD_EINVAL,
+               "log-normal prior needs median > 0 and sigma > 0");
+    RD_CHECK(d->step_space[j] == RD_STEP_LINEAR || d->step_space[j] == RD_STEP_LOG,
+             RD_EINVAL, "unknown step space");
+  }
+  return RD_OK;
+}
+
+}  // namespace rd
+
+using namespace rd;
+
+extern "C" {
+
+const char* rd_last_error(void) { return g_err.c_str(); }
+
+rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
+                            rd_problem** out) {
+  RD_CHECK(out, RD_EINVAL, "out is NULL");
+  *out = nullptr;
+  rd_status vs = validate_desc(desc);
+  if (vs != RD_OK) return vs;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    set_error("no CUDA device available");
+    return RD_ECUDA;
+  }
+  rd_problem* p = new rd_problem();
+  p->desc = *desc;
+  if (p->desc.w_max <= 0) p->desc.w_max = 100.0;
+  p->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    delete p;
+    set_error("cannot query the CUDA device");
+    return RD_ECUDA;
+  }
+  DevProblem& dv = p->dev;
+  memset(&dv, 0, sizeof(dv));
+  dv.dim = desc->dim;
+  dv.n_sizes = desc->n_sizes;
+  dv.n_steps = desc->n_steps;
+  dv.precision = desc->precision;
+  dv.growth = desc->growth;
+  dv.n_params = desc->n_params;
+  dv.tau = desc->tau;
+  dv.w_max = p->desc.w_max;
+  for (int j = 0; j < kNParam; ++j) {
+    dv.param_map[j] = desc->param_map[j];
+    dv.fixed[j] = desc->fixed[j];
+    dv.prior_kind[j] = desc->prior_kind[j];
+    dv.prior_p0[j] = desc->prior_p0[j];
+    dv.prior_p1[j] = desc->prior_p1[j];
+    dv.step_space[j] = desc->step_space[j];
+  }
+  dv.max_n = 0;
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int s = 0; s < desc->n_sizes; ++s) {
+    const int n = desc->nx[s];
+    dv.max_n = std::max(dv.max_n, n);
+    dv.sz[s].n = n;
+    dv.sz[s].npts = desc->dim == 1 ? n : n * n;
+    if (desc->dim == 2) {
+      std::vector<float> c((size_t)n * n), mu(n);
+      for (int k = 0; k < n; ++k) {
+        const double ck = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
+        for (int i = 0; i < n; ++i) c[(size_t)k * n + i] = (float)(ck * cos(pi * k * (i + 0.5) / n));
+        const double sk = sin(pi * k / (2.0 * n));
+        mu[k] = (float)(4.0 * sk * sk);
+      }
+      if (cudaMalloc(&p->cmat[s], sizeof(float) * c.size()) != cudaSuccess ||
+          cudaMalloc(&p->mu[s], sizeof(float) * mu.size()) != cudaSuccess ||
+          cudaMemcpy(p->cmat[s], c.data(), sizeof(float) * c.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(p->mu[s], mu.data(), sizeof(float) * mu.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        rd_problem_destroy(p);
+        set_error("device allocation of solver tables failed");
+        return RD_ENOMEM;
+      }
+      dv.sz[s].cmat = p->cmat[s];
+      dv.sz[s].mu = p->mu[s];
+    }
+  }
+  if (cudaMalloc(&p->ws.queue_counters, sizeof(int) * 2 * kMaxSizes) != cudaSuccess ||
+      cudaMemset(p->ws.queue_counters, 0, sizeof(int) * 2 * kMaxSizes) != cudaSuccess) {
+    rd_problem_destroy(p);
+    set_error("device allocation of the work queue failed");
+    return RD_ENOMEM;
+  }
+  if (ensure_capacity(p, 1024) != RD_OK) {
+    rd_problem_destroy(p);
+    return RD_ENOMEM;
+  }
+  if (setup_solve_simt(desc->dim, dv.max_n) != cudaSuccess) {
+    rd_problem_destroy(p);
+    set_error("cannot configure the 2-D solve kernel's shared memory");
+    return RD_ECUDA;
+  }
+  *out = p;
+  return RD_OK;
+}
+
+rd_status rd_problem_destroy(rd_problem* p) {
+  if (!p) return RD_OK;
+  cudaStreamSynchronize(p->stream);
+  for (int s = 0; s < RD_MAX_SIZES; ++s) {
+    cudaFree(p->ic[s]);
+    cudaFree(p->obs[s]);
+    cudaFree(p->cmat[s]);
+    cudaFree(p->mu[s]);
+  }
+  cudaFree(p->ws.queue_items);
+  cudaFree(p->ws.queue_counters);
+  cudaFree(p->h2d_theta);
+  cudaFree(p->h2d_size);
+  cudaFree(p->d2h_phi);
+  cudaFree(p->d2h_status);
+  delete p;
+  return RD_OK;
+}
+
+rd_status rd_set_stream(rd_problem* p, void* cuda_stream) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  p->stream = (cudaStream_t)cuda_stream;
+  return RD_OK;
+}
+
+rd_status rd_set_initial_state(rd_problem* p, int size_idx, const double* u0,
+                               const double* v0) {
+  RD_CHECK(p && u0 && v0, RD_EINVAL, "NULL argument");
+  RD_CHECK(size_idx >= 0 && size_idx < p->desc.n_sizes, RD_EINVAL, "size_idx out of range");
+  DevSize& S = p->dev.sz[size_idx];
+  const size_t npts = (size_t)S.npts;
+  RD_CUDA(cudaStreamSynchronize(p->stream));
+  cudaFree(p->ic[size_idx]);
+  p->ic[size_idx] = nullptr;
+  if (p->desc.precision == RD_PREC_F64) {
+    RD_CUDA(cudaMalloc(&p->ic[size_idx], sizeof(double) * 2 * npts));
+    double* d = (double*)p->ic[size_idx];
+    RD_CUDA(cudaMemcpy(d, u0, sizeof(double) * npts, cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(d + npts, v0, sizeof(double) * npts, cudaMemcpyHostToDevice));
+    S.u0d = d;
+    S.v0d = d + npts;
+  } else {
+    std::vector<float> h(2 * npts);
+    for (size_t i = 0; i < npts; ++i) {
+      h[i] = (float)u0[i];
+      h[npts + i] = (float)v0[i];
+    }
+    RD_CUDA(cudaMalloc(&p->ic[size_idx], sizeof(float) * 2 * npts));
+    float* d = (float*)p->ic[size_idx];
+    RD_CUDA(cudaMemcpy(d, h.data(), sizeof(float) * 2 * npts, cudaMemcpyHostToDevice));
+    S.u0f = d;
+    S.v0f = d + npts;
+  }
+  p->ic_set[size_idx] = true;
+  p->generation++;
+  return RD_OK;
+}
+
+rd_status rd_set_observations(rd_problem* p, int size_idx, int n_times,
+                              const int* obs_steps, int field_mask,
+                              const double* y, double sigma) {
+  RD_CHECK(p && obs_steps && y, RD_EINVAL, "NULL argument");
+  RD_CHECK(size_idx >= 0 && size_idx < p->desc.n_sizes, RD_EINVAL, "size_idx out of range");
+  RD_CHECK(n_times >= 1 && n_times <= RD_MAX_OBS, RD_EINVAL, "n_times must be in 1..8");
+  RD_CHECK(field_mask >= 1 && field_mask <= 3, RD_EINVAL, "field_mask must be 1, 2 or 3");
+  RD_CHECK(sigma > 0 && isfinite(sigma), RD_EINVAL, "sigma must be positive");
+  for (int o = 0; o < n_times; ++o) {
+    RD_CHECK(obs_steps[o] >= 1 && obs_steps[o] <= p->desc.n_steps, RD_EINVAL,
+             "observation step outside 1..n_steps");
+    RD_CHECK(o == 0 || obs_steps[o] > obs_steps[o - 1], RD_EINVAL,
+             "observation steps must increase");
+  }
+  DevSize& S = p->dev.sz[size_idx];
+  const int nf = (field_mask & 1) + ((field_mask >> 1) & 1);
+  const size_t nval = (size_t)n_times * nf * S.npts;
+  RD_CUDA(cudaStreamSynchronize(p->stream));
+  cudaFree(p->obs[size_idx]);
+  p->obs[size_idx] = nullptr;
+  if (p->desc.precision == RD_PREC_F64) {
+    RD_CUDA(cudaMalloc(&p->obs[size_idx], sizeof(double) * nval));
+    RD_CUDA(cudaMemcpy(p->obs[size_idx], y, sizeof(double) * nval, cudaMemcpyHostToDevice));
+    S.yd = (const double*)p->obs[size_idx];
+  } else {
+    std::vector<float> h(nval);
+    for (size_t i = 0; i < nval; ++i) h[i] = (float)y[i];
+    RD_CUDA(cudaMalloc(&p->obs[size_idx], sizeof(float) * nval));
+    RD_CUDA(cudaMemcpy(p->obs[size_idx], h.data(), sizeof(float) * nval, cudaMemcpyHostToDevice));
+    S.yf = (const float*)p->obs[size_idx];
+  }
+  S.n_obs = n_times;
+  for (int o = 0; o < RD_MAX_OBS; ++o) S.obs_steps[o] = o < n_times ? obs_steps[o] : 0;
+  S.field_mask = field_mask;
+  S.inv_two_sigma2 = 1.0 / (2.0 * sigma * sigma);
+  p->obs_set[size_idx] = true;
+  p->generation++;
+  return RD_OK;
+}
+
+static rd_status check_ready(rd_problem* p) {
+  for (int s = 0; s < p->desc.n_sizes; ++s)
+    RD_CHECK(p->ic_set[s] && p->obs_set[s], RD_ESTATE,
+             "initial state and observations must be set for every grid size");
+  return RD_OK;
+}
+
+rd_status rd_evaluate_batch(rd_problem* p, int B, const double* theta,
+                            const int* size_idx, double* loglik,
+                            uint32_t* status, void* fields) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(B >= 0, RD_EINVAL, "B must be >= 0");
+  if (B == 0) return RD_OK;
+  RD_CHECK(theta && loglik && status, RD_EINVAL, "NULL argument");
+  rd_status r = check_ready(p);
+  if (r != RD_OK) return r;
+  if ((r = ensure_capacity(p, B)) != RD_OK) return r;
+  WorkQueue q = make_queue(p);
+  RD_CUDA(launch_fill_queue(q, B, size_idx, loglik, status, p->stream));
+  RD_CUDA(launch_solve(p, theta, loglik, status, fields));
+  return RD_OK;
+}
+
+rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
+                                 const int* size_idx, double* loglik,
+                                 uint32_t* status) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(B >= 0, RD_EINVAL, "B must be >= 0");
+  if (B == 0) return RD_OK;
+  RD_CHECK(theta && loglik && status, RD_EINVAL, "NULL argument");
+  if (B > p->staging_cap) {
+    RD_CUDA(cudaStreamSynchronize(p->stream));
+    cudaFree(p->h2d_theta);
+    cudaFree(p->h2d_size);
+    cudaFree(p->d2h_phi);
+    cudaFree(p->d2h_status);
+    p->h2d_theta = nullptr;
+    p->h2d_size = nullptr;
+    p->d2h_phi = nullptr;
+    p->d2h_status = nullptr;
+    p->staging_cap = 0;
+    RD_CUDA(cudaMalloc(&p->h2d_theta, sizeof(double) * (size_t)B * p->desc.n_params));
+    RD_CUDA(cudaMalloc(&p->h2d_size, sizeof(int) * (size_t)B));
+    RD_CUDA(cudaMalloc(&p->d2h_phi, sizeof(double) * (size_t)B));
+    RD_CUDA(cudaMalloc(&p->d2h_status, sizeof(uint32_t) * (size_t)B));
+    p->staging_cap = B;
+  }
+  RD_CUDA(cudaMemcpyAsync(p->h2d_theta, theta, sizeof(double) * (size_t)B * p->desc.n_params,
+                          cudaMemcpyHostToDevice, p->stream));
+  if (size_idx)
+    RD_CUDA(cudaMemcpyAsync(p->h2d_size, size_idx, sizeof(int) * (size_t)B,
+                            cudaMemcpyHostToDevice, p->stream));
+  rd_status r = rd_evaluate_batch(p, B, p->h2d_theta, size_idx ? p->h2d_size : nullptr,
+                                  p->d2h_phi, p->d2h_status, nullptr);
+  if (r != RD_OK) return r;
+  RD_CUDA(cudaMemcpyAsync(loglik, p->d2h_phi, sizeof(double) * (size_t)B,
+                          cudaMemcpyDeviceToHost, p->stream));
+  RD_CUDA(cudaMemcpyAsync(status, p->d2h_status, sizeof(uint32_t) * (size_t)B,
+                          cudaMemcpyDeviceToHost, p->stream));
+  RD_CUDA(cudaStreamSynchronize(p->stream));
+  return RD_OK;
+}
+
+rd_status rd_sync(rd_problem* p) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CUDA(cudaStreamSynchronize(p->stream));
+  return RD_OK;
+}
+
+// ------------------------------------------------------------------ chains
+rd_status rd_chains_destroy(rd_chains* c) {
+  if (!c) return RD_OK;
+  if (c->pb) cudaStreamSynchronize(c->pb->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  cudaFree(c->theta);
+  cudaFree(c->phi);
+  cudaFree(c->phit);
+  cudaFree(c->lp);
+  cudaFree(c->size_idx);
+  cudaFree(c->prop);
+  cudaFree(c->prop_phi);
+  cudaFree(c->prop_phit);
+  cudaFree(c->prop_lp);
+  cudaFree(c->prop_status);
+  cudaFree(c->samples);
+  cudaFree(c->counters);
+  cudaFree(c->ctl);
+  delete c;
+  return RD_OK;
+}
+
+rd_status rd_chains_create(rd_problem* p, int n_chains, const double* theta0,
+                           uint64_t seed, const double* step,
+                           const int* size_idx, int capacity, rd_chains** out) {
+  RD_CHECK(p && theta0 && step && out, RD_EINVAL, "NULL argument");
+  *out = nullptr;
+  RD_CHECK(n_chains >= 1, RD_EINVAL, "n_chains must be >= 1");
+  RD_CHECK(capacity >= 1, RD_EINVAL, "capacity must be >= 1");
+  rd_status r = check_ready(p);
+  if (r != RD_OK) return r;
+  if (size_idx)
+    for (int i = 0; i < n_chains; ++i)
+      RD_CHECK(size_idx[i] >= 0 && size_idx[i] < p->desc.n_sizes, RD_EINVAL,
+               "size_idx out of range");
+  if ((r = ensure_capacity(p, n_chains)) != RD_OK) return r;
+  rd_chains* c = new rd_chains();
+  c->pb = p;
+  c->C = n_chains;
+  c->P = p->desc.n_params;
+  c->seed = seed;
+  c->capacity = capacity;
+  for (int j = 0; j < c->P; ++j) c->step[j] = step[j];
+  const size_t C = (size_t)n_chains, P = (size_t)c->P;
+  bool ok = cudaMalloc(&c->theta, sizeof(double) * C * P) == cudaSuccess &&
+            cudaMalloc(&c->phi, sizeof(double) * C) == cudaSuccess &&
+            cudaMalloc(&c->phit, sizeof(double) * C) == cudaSuccess &&
+            cudaMalloc(&c->lp, sizeof(double) * C) == cudaSuccess &&
+            cudaMalloc(&c->size_idx, sizeof(int) * C) == cudaSuccess &&
+            cudaMalloc(&c->prop, sizeof(double) * C * P) == cudaSuccess &&
+            cudaMalloc(&c->prop_phi, sizeof(double) * C) == cudaSuccess &&
+            cudaMalloc(&c->prop_phit, sizeof(double) * C) == cudaSuccess &&
+            cudaMalloc(&c->prop_lp, sizeof(double) * C) == cudaSuccess &&
+            cudaMalloc(&c->prop_status, sizeof(uint32_t) * C) == cudaSuccess &&
+            cudaMalloc(&c->samples, sizeof(double) * (size_t)capacity * P * C) == cudaSuccess &&
+            cudaMalloc(&c->counters, sizeof(unsigned long long) * 4 * C) == cudaSuccess &&
+            cudaMalloc(&c->ctl, sizeof(int) * 4) == cudaSuccess;
+  if (!ok) {
+    rd_chains_destroy(c);
+    set_error("device allocation for chains failed");
+    return RD_ENOMEM;
+  }
+  std::vector<int> sz(C, 0);
+  if (size_idx) sz.assign(size_idx, size_idx + C);
+  if (cudaMemcpy(c->theta, theta0, sizeof(double) * C * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->size_idx, sz.data(), sizeof(int) * C, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->counters, 0, sizeof(unsigned long long) * 4 * C) != cudaSuccess ||
+      cudaMemset(c->ctl, 0, sizeof(int) * 4) != cudaSuccess ||
+      cudaMemset(c->phit, 0, sizeof(double) * C) != cudaSuccess) {
+    rd_chains_destroy(c);
+    set_error("initialising chain state failed");
+    return RD_ECUDA;
+  }
+  if (launch_chain_init(c) != cudaSuccess) {
+    rd_chains_destroy(c);
+    set_error("launching the initial solves failed");
+    return RD_ECUDA;
+  }
+  *out = c;
+  return RD_OK;
+}
+
+static rd_status capture_step_graph(rd_chains* c) {
+  cudaStream_t cs;
+  RD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = c->pb->stream;
+  c->pb->stream = cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e2 = e == cudaSuccess ? launch_chain_step(c) : e;
+  cudaError_t e3 = e == cudaSuccess ? cudaStreamEndCapture(cs, &g) : e;
+  c->pb->stream = saved;
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    set_error(std::string("capturing the MCMC step graph failed: ") +
+              cudaGetErrorString(e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3)));
+    return RD_ECUDA;
+  }
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_error(std::string("instantiating the MCMC step graph failed: ") + cudaGetErrorString(e));
+    return RD_ECUDA;
+  }
+  c->graph_ready = true;
+  c->graph_generation = c->pb->generation;
+  return RD_OK;
+}
+
+rd_status rd_chains_run(rd_chains* c, int n_steps) {
+  RD_CHECK(c, RD_EINVAL, "chains is NULL");
+  RD_CHECK(n_steps >= 0, RD_EINVAL, "n_steps must be >= 0");
+  RD_CHECK(c->ring_host + n_steps <= c->capacity, RD_ESTATE,
+           "sample buffer full: call rd_chains_read_samples first");
+  if (!c->graph_ready || c->graph_generation != c->pb->generation) {
+    RD_CUDA(cudaStreamSynchronize(c->pb->stream));
+    rd_status r = capture_step_graph(c);
+    if (r != RD_OK) return r;
+  }
+  for (int s = 0; s < n_steps; ++s) RD_CUDA(cudaGraphLaunch(c->graph, c->pb->stream));
+  c->ring_host += n_steps;
+  return RD_OK;
+}
+
+rd_status rd_chains_read_samples(rd_chains* c, double* out, size_t cap_steps,
+                                 size_t* n_written, double* counters) {
+  RD_CHECK(c, RD_EINVAL, "chains is NULL");
+  cudaStream_t st = c->pb->stream;
+  const size_t per = (size_t)c->P * c->C;
+  size_t n = std::min((size_t)c->ring_host, out ? cap_steps : 0);
+  if (n > 0) RD_CUDA(cudaMemcpyAsync(out, c->samples, sizeof(double) * per * n,
+                                     cudaMemcpyDeviceToHost, st));
+  if (counters) {
+    std::vector<unsigned long long> h(4 * (size_t)c->C);
+    RD_CUDA(cudaMemcpyAsync(h.data(), c->counters, sizeof(unsigned long long) * h.size(),
+                            cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < 4; ++k) {
+      double s = 0;
+      for (int i = 0; i < c->C; ++i) s += (double)h[(size_t)k * c->C + i];
+      counters[k] = s;
+    }
+  }
+  RD_CUDA(cudaStreamSynchronize(st));
+  if (n < (size_t)c->ring_host && n > 0) {
+    // move the unread tail to the front of the ring in chunks of n samples,
+    // so that no copy has overlapping source and destination
+    for (size_t k = n; k < (size_t)c->ring_host; k += n) {
+      const size_t len = std::min(n, (size_t)c->ring_host - k);
+      RD_CUDA(cudaMemcpyAsync(c->samples + per * (k - n), c->samples + per * k,
+                              sizeof(double) * per * len, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  c->ring_host -= (int)n;
+  const int ring = c->ring_host;
+  RD_CUDA(cudaMemcpyAsync(c->ctl + 1, &ring, sizeof(int), cudaMemcpyHostToDevice, st));
+  RD_CUDA(cudaStreamSynchronize(st));
+  if (n_written) *n_written = n;
+  return RD_OK;
+}
+
+rd_status rd_chains_get_state(rd_chains* c, double* theta, double* phi) {
+  RD_CHECK(c, RD_EINVAL, "chains is NULL");
+  cudaStream_t st = c->pb->stream;
+  if (theta)
+    RD_CUDA(cudaMemcpyAsync(theta, c->theta, sizeof(double) * c->C * c->P,
+                            cudaMemcpyDeviceToHost, st));
+  if (phi) RD_CUDA(cudaMemcpyAsync(phi, c->phi, sizeof(double) * c->C, cudaMemcpyDeviceToHost, st));
+  RD_CUDA(cudaStreamSynchronize(st));
+  return RD_OK;
+}
+
+namespace {
+struct CkptHeader {
+  uint32_t magic;  // 'RDCK'
+  uint32_t version;
+  int32_t C, P;
+  uint64_t seed;
+  int32_t step;
+  int32_t pad;
+};
+}  // namespace
+
+rd_status rd_chains_checkpoint(rd_chains* c, void* buf, size_t cap, size_t* n) {
+  RD_CHECK(c && n, RD_EINVAL, "NULL argument");
+  const size_t C = (size_t)c->C, P = (size_t)c->P;
+  const size_t need = sizeof(CkptHeader) + sizeof(double) * (C * P + 3 * C) +
+                      sizeof(unsigned long long) * 4 * C;
+  *n = need;
+  if (!buf) return RD_OK;
+  RD_CHECK(cap >= need, RD_EINVAL, "checkpoint buffer too small");
+  cudaStream_t st = c->pb->stream;
+  CkptHeader h;
+  int ctl[4];
+  RD_CUDA(cudaMemcpyAsync(ctl, c->ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+  char* q = (char*)buf + sizeof(CkptHeader);
+  RD_CUDA(cudaMemcpyAsync(q, c->theta, sizeof(double) * C * P, cudaMemcpyDeviceToHost, st));
+  q += sizeof(double) * C * P;
+  RD_CUDA(cudaMemcpyAsync(q, c->phi, sizeof(double) * C, cudaMemcpyDeviceToHost, st));
+  q += sizeof(double) * C;
+  RD_CUDA(cudaMemcpyAsync(q, c->phit, sizeof(double) * C, cudaMemcpyDeviceToHost, st));
+  q += sizeof(double) * C;
+  RD_CUDA(cudaMemcpyAsync(q, c->lp, sizeof(double) * C, cudaMemcpyDeviceToHost, st));
+  q += sizeof(double) * C;
+  RD_CUDA(cudaMemcpyAsync(q, c->counters, sizeof(unsigned long long) * 4 * C,
+                          cudaMemcpyDeviceToHost, st));
+  RD_CUDA(cudaStreamSynchronize(st));
+  h.magic = 0x4B434452u;
+  h.version = 1;
+  h.C = c->C;
+  h.P = c->P;
+  h.seed = c->seed;
+  h.step = ctl[0];
+  h.pad = 0;
+  memcpy(buf, &h, sizeof(h));
+  return RD_OK;
+}
+
+rd_status rd_chains_restore(rd_chains* c, const void* buf, size_t n) {
+  RD_CHECK(c && buf, RD_EINVAL, "NULL argument");
+  const size_t C = (size_t)c->C, P = (size_t)c->P;
+  const size_t need = sizeof(CkptHeader) + sizeof(double) * (C * P + 3 * C) +
+                      sizeof(unsigned long long) * 4 * C;
+  RD_CHECK(n >= need, RD_EINVAL, "checkpoint too short");
+  CkptHeader h;
+  memcpy(&h, buf, sizeof(h));
+  RD_CHECK(h.magic == 0x4B434452u && h.version == 1, RD_EINVAL, "not a chain checkpoint");
+  RD_CHECK(h.C == c->C && h.P == c->P && h.seed == c->seed, RD_EINVAL,
+           "checkpoint is for different chains (C, P or seed differ)");
+  cudaStream_t st = c->pb->stream;
+  const char* q = (const char*)buf + sizeof(CkptHeader);
+  RD_CUDA(cudaMemcpyAsync(c->theta, q, sizeof(double) * C * P, cudaMemcpyHostToDevice, st));
+  q += sizeof(double) * C * P;
+  RD_CUDA(cudaMemcpyAsync(c->phi, q, sizeof(double) * C, cudaMemcpyHostToDevice, st));
+  q += sizeof(double) * C;
+  RD_CUDA(cudaMemcpyAsync(c->phit, q, sizeof(double) * C, cudaMemcpyHostToDevice, st));
+  q += sizeof(double) * C;
+  RD_CUDA(cudaMemcpyAsync(c->lp, q, sizeof(double) * C, cudaMemcpyHostToDevice, st));
+  q += sizeof(double) * C;
+  RD_CUDA(cudaMemcpyAsync(c->counters, q, sizeof(unsigned long long) * 4 * C,
+                          cudaMemcpyHostToDevice, st));
+  int ctl[4] = {h.step, 0, 0, 0};
+  RD_CUDA(cudaMemcpyAsync(c->ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st));
+  RD_CUDA(cudaStreamSynchronize(st));
+  c->ring_host = 0;
+  return RD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// rd_internal.h -- host-side objects behind the C ABI handles and the kernel
+// launchers shared between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rdbayes.h"
+#include "rd_common.cuh"
+
+namespace rd {
+
+void set_error(const std::string& msg);
+
+// Problem-level device workspace: work lists and per-proposal outputs of the
+// chain sampler's exact solves.
+struct Workspace {
+  int* queue_items = nullptr;   // [n_sizes][capacity]
+  int* queue_counters = nullptr;  // [2 * kMaxSizes]: counts, pops
+  int capacity = 0;
+};
+
+}  // namespace rd
+
+struct rd_problem {
+  rd_problem_desc desc;
+  rd::DevProblem dev;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n_sm = 0;
+  bool ic_set[RD_MAX_SIZES] = {false, false, false, false};
+  bool obs_set[RD_MAX_SIZES] = {false, false, false, false};
+  // per-size device buffers (owned)
+  void* ic[RD_MAX_SIZES] = {nullptr, nullptr, nullptr, nullptr};
+  void* obs[RD_MAX_SIZES] = {nullptr, nullptr, nullptr, nullptr};
+  float* cmat[RD_MAX_SIZES] = {nullptr, nullptr, nullptr, nullptr};
+  float* mu[RD_MAX_SIZES] = {nullptr, nullptr, nullptr, nullptr};
+  rd::Workspace ws;
+  // bumped whenever a device buffer that a captured graph may reference is
+  // replaced; chains re-capture their step graph when it changes
+  int generation = 0;
+  int solver_per_size[RD_MAX_SIZES] = {0, 0, 0, 0};
+  // staging for rd_evaluate_batch_host
+  double* h2d_theta = nullptr;
+  int* h2d_size = nullptr;
+  double* d2h_phi = nullptr;
+  uint32_t* d2h_status = nullptr;
+  int staging_cap = 0;
+};
+
+struct rd_chains {
+  rd_problem* pb = nullptr;
+  int C = 0;
+  int P = 0;
+  uint64_t seed = 0;
+  int capacity = 0;
+  int ring_host = 0;  // samples in the device ring (host mirror)
+  double step[RD_NPARAM] = {0, 0, 0, 0, 0};
+  // device state
+  double* theta = nullptr;      // [C][P]
+  double* phi = nullptr;        // [C]
+  double* phit = nullptr;       // [C] surrogate Phi~ (DA only)
+  double* lp = nullptr;         // [C] log prior (+ log Jacobian) in step space
+  int* size_idx = nullptr;      // [C]
+  double* prop = nullptr;       // [C][P] proposals
+  double* prop_phi = nullptr;   // [C]
+  double* prop_phit = nullptr;  // [C]
+  double* prop_lp = nullptr;    // [C]
+  uint32_t* prop_status = nullptr;  // [C]
+  double* samples = nullptr;    // [capacity][P][C]
+  unsigned long long* counters = nullptr;  // [4][C]: proposals, pass1, accepted, solves
+  int* ctl = nullptr;           // [0]: step index, [1]: ring fill
+  cudaGraphExec_t graph = nullptr;
+  bool graph_ready = false;
+  int graph_generation = -1;
+};
+
+namespace rd {
+
+cudaError_t launch_fill_queue(const WorkQueue& q, int B, const int* size_idx,
+                              double* phi, uint32_t* status, cudaStream_t st);
+cudaError_t launch_solve_simt(const DevProblem& pb, const WorkQueue& q,
+                              const double* theta, double* phi, uint32_t* status,
+                              void* fields, int grid, cudaStream_t st);
+cudaError_t setup_solve_simt(int dim, int max_n);
+int grid_solve_simt(int dim, int max_n, int n_sm);
+size_t simt2d_smem_bytes(int n);
+
+WorkQueue make_queue(const rd_problem* p);
+cudaError_t launch_solve(rd_problem* p, const double* theta, double* phi,
+                         uint32_t* status, void* fields);
+
+// chains
+cudaError_t launch_chain_init(rd_chains* c);
+cudaError_t launch_chain_step(rd_chains* c);
+
+}  // namespace rd

@@ -1,0 +1,214 @@
+// rd_mcmc.cu -- lock-step random-walk Metropolis chains on the device.
+//
+// One step of Algorithm 1 for every chain: draw a proposal from the symmetric
+// Gaussian random walk, evaluate the prior, solve the forward problem for the
+// proposals inside the prior's support, and accept with probability
+// min(1, exp(-Phi(x_bar) + log mu0(x_bar) + Phi(x) - log mu0(x))).  The prior
+// ratio is the paper's rule for a non-flat prior (eq. (bayes)); parameters
+// stepped in log space carry the Jacobian theta in their density.
+// Random numbers: Philox4x32-10 at counters (chain, step, 0|1, 0), key = seed;
+// u_0..u_5 -> Box-Muller normals, u_6 -> acceptance uniform.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "rd_common.cuh"
+#include "rd_internal.h"
+
+namespace rd {
+
+struct ChainView {
+  int C, P;
+  uint64_t seed;
+  double step[kNParam];
+  double* theta;
+  double* phi;
+  double* phit;
+  double* lp;
+  const int* size_idx;
+  double* prop;
+  double* prop_phi;
+  double* prop_phit;
+  double* prop_lp;
+  uint32_t* prop_status;
+  double* samples;
+  unsigned long long* counters;
+  int* ctl;
+};
+
+static ChainView view_of(const rd_chains* c) {
+  ChainView v;
+  v.C = c->C;
+  v.P = c->P;
+  v.seed = c->seed;
+  for (int j = 0; j < kNParam; ++j) v.step[j] = c->step[j];
+  v.theta = c->theta;
+  v.phi = c->phi;
+  v.phit = c->phit;
+  v.lp = c->lp;
+  v.size_idx = c->size_idx;
+  v.prop = c->prop;
+  v.prop_phi = c->prop_phi;
+  v.prop_phit = c->prop_phit;
+  v.prop_lp = c->prop_lp;
+  v.prop_status = c->prop_status;
+  v.samples = c->samples;
+  v.counters = c->counters;
+  v.ctl = c->ctl;
+  return v;
+}
+
+// log mu0(theta) + sum of log |d theta / d eta| over log-stepped parameters;
+// -inf outside the support.  Constants are dropped.
+__device__ double log_prior_eta(const DevProblem& pb, const double* th) {
+  double lp = 0.0;
+  for (int j = 0; j < pb.n_params; ++j) {
+    const double t = th[j];
+    double lpj;
+    if (pb.prior_kind[j] == RD_PRIOR_UNIFORM) {
+      lpj = (t >= pb.prior_p0[j] && t <= pb.prior_p1[j]) ? 0.0 : -(double)INFINITY;
+    } else {
+      if (t > 0.0) {
+        const double lt = log(t);
+        const double z = (lt - log(pb.prior_p0[j])) / pb.prior_p1[j];
+        lpj = -lt - 0.5 * z * z;
+      } else {
+        lpj = -(double)INFINITY;
+      }
+    }
+    if (pb.step_space[j] == RD_STEP_LOG) lpj = lpj + log(t > 0.0 ? t : 1.0);
+    lp += lpj;
+  }
+  return lp;
+}
+
+__device__ __forceinline__ void chain_normals(const double u[8], double xi[6]) {
+  const double two_pi = 6.283185307179586476925286766559;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double rad = sqrt(-2.0 * log(u[2 * j]));
+    const double ang = two_pi * u[2 * j + 1];
+    xi[2 * j] = rad * cos(ang);
+    xi[2 * j + 1] = rad * sin(ang);
+  }
+}
+
+__device__ __forceinline__ void queue_push(const WorkQueue& q, int s, int item) {
+  const int i = atomicAdd(&q.counts[s], 1);
+  q.items[(size_t)s * q.capacity + i] = item;
+}
+
+__global__ void k_chain_init(DevProblem pb, WorkQueue q, ChainView v) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.C) return;
+  double th[kNParam];
+  for (int j = 0; j < v.P; ++j) th[j] = v.theta[(size_t)c * v.P + j];
+  const double lp = log_prior_eta(pb, th);
+  v.lp[c] = lp;
+  if (isfinite(lp)) {
+    queue_push(q, v.size_idx[c], c);
+  } else {
+    v.phi[c] = (double)INFINITY;
+    v.prop_status[c] = RD_P_OUT_OF_SUPPORT;
+  }
+}
+
+__global__ void k_chain_propose(DevProblem pb, WorkQueue q, ChainView v) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.C) return;
+  const uint32_t step = (uint32_t)v.ctl[0];
+  double u[8], xi[6];
+  chain_uniforms(v.seed, (uint32_t)c, step, u);
+  chain_normals(u, xi);
+  double th[kNParam];
+  for (int j = 0; j < v.P; ++j) {
+    const double t = v.theta[(size_t)c * v.P + j];
+    double tb;
+    if (pb.step_space[j] == RD_STEP_LOG)
+      tb = exp(log(t) + v.step[j] * xi[j]);
+    else
+      tb = t + v.step[j] * xi[j];
+    th[j] = tb;
+    v.prop[(size_t)c * v.P + j] = tb;
+  }
+  const double lp = log_prior_eta(pb, th);
+  v.prop_lp[c] = lp;
+  if (isfinite(lp)) {
+    v.prop_status[c] = 0u;
+    queue_push(q, v.size_idx[c], c);
+  } else {
+    v.prop_status[c] = RD_P_OUT_OF_SUPPORT;
+    v.prop_phi[c] = (double)INFINITY;
+  }
+}
+
+__global__ void k_chain_accept(DevProblem pb, ChainView v) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.C) return;
+  const uint32_t step = (uint32_t)v.ctl[0];
+  const int slot = v.ctl[1];
+  double u[8];
+  chain_uniforms(v.seed, (uint32_t)c, step, u);
+  const uint32_t st = v.prop_status[c];
+  bool acc = false;
+  if (st == 0u) {
+    const double la = (-v.prop_phi[c] + v.prop_lp[c]) - (-v.phi[c] + v.lp[c]);
+    acc = log(u[6]) < la;
+  }
+  if (acc) {
+    for (int j = 0; j < v.P; ++j)
+      v.theta[(size_t)c * v.P + j] = v.prop[(size_t)c * v.P + j];
+    v.phi[c] = v.prop_phi[c];
+    v.lp[c] = v.prop_lp[c];
+  }
+  for (int j = 0; j < v.P; ++j)
+    v.samples[((size_t)slot * v.P + j) * v.C + c] = v.theta[(size_t)c * v.P + j];
+  v.counters[c] += 1ull;
+  v.counters[(size_t)v.C + c] += (st != RD_P_OUT_OF_SUPPORT) ? 1ull : 0ull;
+  v.counters[(size_t)2 * v.C + c] += acc ? 1ull : 0ull;
+  v.counters[(size_t)3 * v.C + c] += (st != RD_P_OUT_OF_SUPPORT) ? 1ull : 0ull;
+}
+
+// Ends one MCMC step: advances the step counter and the sample ring, and
+// empties the work lists for the next step.
+__global__ void k_chain_advance(WorkQueue q, int* ctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ctl[0] += 1;
+    ctl[1] += 1;
+  }
+  if (threadIdx.x < 2 * kMaxSizes) q.counts[threadIdx.x] = 0;  // counts, pops
+}
+
+cudaError_t launch_chain_init(rd_chains* c) {
+  rd_problem* p = c->pb;
+  WorkQueue q = make_queue(p);
+  ChainView v = view_of(c);
+  cudaError_t e = cudaMemsetAsync(q.counts, 0, 2 * kMaxSizes * sizeof(int), p->stream);
+  if (e != cudaSuccess) return e;
+  k_chain_init<<<(c->C + 127) / 128, 128, 0, p->stream>>>(p->dev, q, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_solve(p, c->theta, c->phi, c->prop_status, nullptr);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(q.counts, 0, 2 * kMaxSizes * sizeof(int), p->stream);
+}
+
+// Enqueues one full MCMC step (propose, exact solves, accept, advance).
+cudaError_t launch_chain_step(rd_chains* c) {
+  rd_problem* p = c->pb;
+  WorkQueue q = make_queue(p);
+  ChainView v = view_of(c);
+  const int blocks = (c->C + 127) / 128;
+  // the work lists may hold counts from an rd_evaluate_batch call in between
+  cudaError_t e = cudaMemsetAsync(q.counts, 0, 2 * kMaxSizes * sizeof(int), p->stream);
+  if (e != cudaSuccess) return e;
+  k_chain_propose<<<blocks, 128, 0, p->stream>>>(p->dev, q, v);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_solve(p, c->prop, c->prop_phi, c->prop_status, nullptr);
+  if (e != cudaSuccess) return e;
+  k_chain_accept<<<blocks, 128, 0, p->stream>>>(p->dev, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_chain_advance<<<1, 32, 0, p->stream>>>(q, c->ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace rd

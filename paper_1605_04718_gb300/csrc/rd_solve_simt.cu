@@ -1,0 +1,433 @@
+// rd_solve_simt.cu -- forward solve G(p) and log-likelihood Phi(p; y) on CUDA
+// cores: the 1-D FP64 Thomas path and the 2-D FP32 eigenbasis path.
+//
+// Both follow the IMEX Euler step of Sec. 3.1.1 with the reaction explicit
+// and diffusion plus the dilution term of eq. (schnakenberg) implicit:
+//   r_u = u + tau gamma (a - u + u^2 v),   r_v = v + tau gamma (b - u^2 v)
+//   [(1 + tau m r) I - tau D rho_n^-2 Lap_h] w^{n+1} = r_w,  D = 1 (u), d (v)
+// with the cell-centred Neumann Laplacian, and accumulate
+// Phi = sum (y - w)^2 / (2 sigma^2) (eq. (logl)) at the observation steps.
+// Growth factors rho_n = exp(r n tau) are formed in FP64 once per step and
+// rounded once to the field precision.
+//
+// The persistent kernels pop proposals from per-size work lists (largest grid
+// first) until the lists are empty, so one launch covers any mix of sizes.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "rd_common.cuh"
+#include "rd_internal.h"
+
+namespace rd {
+
+// ---------------------------------------------------------------------------
+// 1-D, FP64, one thread per proposal: Thomas algorithm on the tridiagonal
+// Neumann matrix (diagonal alpha + 2 beta, alpha + beta in the two boundary
+// rows, off-diagonals -beta).
+// ---------------------------------------------------------------------------
+template <int NMAX>
+__device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
+                             const double th[5], double* phi_out,
+                             uint32_t* st_out, double* fields_out) {
+  double u[NMAX], v[NMAX], ru[NMAX], rv[NMAX], cu[NMAX], cv[NMAX];
+  const int n = S.n;
+  for (int i = 0; i < n; ++i) {
+    u[i] = S.u0d[i];
+    v[i] = S.v0d[i];
+  }
+  const double a = th[0], b = th[1], d = th[2], g = th[3], r = th[4];
+  const double tau = pb.tau, h2inv = (double)n * n;
+  const int nfo = (S.field_mask & 1) + ((S.field_mask >> 1) & 1);
+  double phi = 0.0;
+  bool bad = false;
+  int next_obs = 0;
+  for (int step = 0; step < pb.n_steps; ++step) {
+    const double rho = exp(r * (double)step * tau);
+    const double alpha = 1.0 + tau * 1.0 * r;  // m = 1 in 1-D
+    const double bu = tau / (rho * rho) * h2inv;
+    const double bv = tau * d / (rho * rho) * h2inv;
+    for (int i = 0; i < n; ++i) {
+      const double uu = u[i], vv = v[i];
+      const double u2v = uu * uu * vv;
+      ru[i] = uu + tau * g * (a - uu + u2v);
+      rv[i] = vv + tau * g * (b - u2v);
+    }
+    if (n == 1) {
+      u[0] = ru[0] / alpha;
+      v[0] = rv[0] / alpha;
+    } else {
+      // forward elimination (cu, cv: modified super-diagonal; ru, rv: rhs)
+      double den_u = alpha + bu, den_v = alpha + bv;
+      cu[0] = -bu / den_u;
+      cv[0] = -bv / den_v;
+      ru[0] /= den_u;
+      rv[0] /= den_v;
+      for (int i = 1; i < n; ++i) {
+        const double du = (i == n - 1 ? alpha + bu : alpha + 2.0 * bu) + bu * cu[i - 1];
+        const double dv = (i == n - 1 ? alpha + bv : alpha + 2.0 * bv) + bv * cv[i - 1];
+        cu[i] = -bu / du;
+        cv[i] = -bv / dv;
+        ru[i] = (ru[i] + bu * ru[i - 1]) / du;
+        rv[i] = (rv[i] + bv * rv[i - 1]) / dv;
+      }
+      u[n - 1] = ru[n - 1];
+      v[n - 1] = rv[n - 1];
+      for (int i = n - 2; i >= 0; --i) {
+        u[i] = ru[i] - cu[i] * u[i + 1];
+        v[i] = rv[i] - cv[i] * v[i + 1];
+      }
+    }
+    if (next_obs < S.n_obs && step + 1 == S.obs_steps[next_obs]) {
+      const double* yo = S.yd + (size_t)next_obs * nfo * n;
+      int fo = 0;
+      for (int f = 0; f < 2; ++f) {
+        if (!(S.field_mask & (1 << f))) continue;
+        const double* w = f ? v : u;
+        for (int i = 0; i < n; ++i) {
+          if (!isfinite(w[i]) || fabs(w[i]) > pb.w_max) bad = true;
+          const double e = yo[(size_t)fo * n + i] - w[i];
+          phi += e * e;
+        }
+        ++fo;
+      }
+      ++next_obs;
+    }
+  }
+  *st_out = bad ? (uint32_t)RD_P_NONFINITE : 0u;
+  *phi_out = bad ? (double)INFINITY : phi * S.inv_two_sigma2;
+  if (fields_out) {
+    for (int i = 0; i < n; ++i) {
+      fields_out[i] = u[i];
+      fields_out[n + i] = v[i];
+    }
+  }
+}
+
+template <int NMAX>
+__global__ void k_solve1d_f64(DevProblem pb, WorkQueue q, const double* theta,
+                              double* phi, uint32_t* status, double* fields,
+                              size_t field_stride) {
+  for (;;) {
+    int s;
+    const int b = queue_pop(q, &s);
+    if (b < 0) break;
+    double th[5];
+    full_theta(pb, theta + (size_t)b * pb.n_params, th);
+    double* fo = fields ? fields + (size_t)b * field_stride : nullptr;
+    solve1d_item<NMAX>(pb, pb.sz[s], th, &phi[b], &status[b], fo);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2-D, FP32 fields, one CTA of 256 threads per proposal with u, v and the DCT
+// matrix resident in shared memory for the whole time loop.
+//
+// Implicit solve by diagonalisation in the Neumann eigenbasis (orthonormal
+// DCT-II, C[k][i] = c_k cos(pi k (i + 1/2) / N)):
+//   P = W C^T, Q = C P, S = Q / (alpha + beta (mu_l + mu_k)), W1 = C^T S,
+//   W = W1 C,   mu_k = 4 sin^2(pi k / (2N)), beta = tau D / (rho^2 h^2).
+// Each product is an N x N x N GEMM from shared memory with 16 x 16 threads,
+// thread (ty, tx) owning rows ty + 16 i and columns tx + 16 j.  Rows are
+// padded to N + 1 floats so that every operand load is conflict-free.
+// ---------------------------------------------------------------------------
+constexpr int kSimtThreads = 256;
+
+template <int N>
+constexpr size_t simt_smem_bytes() {
+  return (size_t)3 * N * (N + 1) * sizeof(float);
+}
+
+// acc[i][j] = sum_k A(ty + 16 i, k) B(k, tx + 16 j), A(m, k) = pa[m*SAM + k*SAK],
+// B(k, n) = pb[k*SBK + n*SBN].
+template <int N, int SAM, int SAK, int SBK, int SBN>
+__device__ __forceinline__ void smem_gemm(const float* __restrict__ pa,
+                                          const float* __restrict__ pb,
+                                          float (&acc)[N / 16][N / 16], int ty,
+                                          int tx) {
+  constexpr int TM = N / 16;
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < N; ++k) {
+    float av[TM], bv[TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) av[i] = pa[(ty + 16 * i) * SAM + k * SAK];
+#pragma unroll
+    for (int j = 0; j < TM; ++j) bv[j] = pb[k * SBK + (tx + 16 * j) * SBN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TM; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_tile(float* W, const float (&acc)[N / 16][N / 16],
+                                           int ty, int tx) {
+  constexpr int TM = N / 16, NP = N + 1;
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) W[(ty + 16 * i) * NP + tx + 16 * j] = acc[i][j];
+}
+
+// In place: W <- [alpha I - beta Lap_h]^-1 W.
+template <int N>
+__device__ __forceinline__ void implicit_solve_simt(float* W, const float* Cm,
+                                                    float alpha, float beta,
+                                                    const float (&mur)[N / 16],
+                                                    const float (&muc)[N / 16],
+                                                    int ty, int tx) {
+  constexpr int TM = N / 16, NP = N + 1;
+  float acc[TM][TM];
+  // P[y][k] = sum_x W[y][x] C[k][x]
+  smem_gemm<N, NP, 1, 1, NP>(W, Cm, acc, ty, tx);
+  __syncthreads();
+  store_tile<N>(W, acc, ty, tx);
+  __syncthreads();
+  // Q[l][k] = sum_y C[l][y] P[y][k];  S = Q / (alpha + beta (mu_l + mu_k))
+  smem_gemm<N, NP, 1, NP, 1>(Cm, W, acc, ty, tx);
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) acc[i][j] = acc[i][j] / fmaf(beta, mur[i] + muc[j], alpha);
+  __syncthreads();
+  store_tile<N>(W, acc, ty, tx);
+  __syncthreads();
+  // W1[y][k] = sum_l C[l][y] S[l][k]
+  smem_gemm<N, 1, NP, NP, 1>(Cm, W, acc, ty, tx);
+  __syncthreads();
+  store_tile<N>(W, acc, ty, tx);
+  __syncthreads();
+  // W[y][x] = sum_k W1[y][k] C[k][x]
+  smem_gemm<N, NP, 1, NP, 1>(W, Cm, acc, ty, tx);
+  __syncthreads();
+  store_tile<N>(W, acc, ty, tx);
+  __syncthreads();
+}
+
+// FP64 sum over the CTA; result valid in thread 0.
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+template <int N>
+__device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
+                                  const double th[5], float* sm, double* red,
+                                  double* phi_out, uint32_t* st_out,
+                                  float* fields_out) {
+  constexpr int TM = N / 16, NP = N + 1, NPTS = N * N;
+  float* U = sm;
+  float* V = sm + N * NP;
+  float* Cm = sm + 2 * N * NP;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  for (int i = tid; i < NPTS; i += kSimtThreads) {
+    const int r = i / N, c = i - r * N;
+    Cm[r * NP + c] = S.cmat[i];
+    U[r * NP + c] = S.u0f[i];
+    V[r * NP + c] = S.v0f[i];
+  }
+  float mur[TM], muc[TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    mur[i] = S.mu[ty + 16 * i];
+    muc[i] = S.mu[tx + 16 * i];
+  }
+  const double d = th[2], r = th[4], tau = pb.tau;
+  const float fa = (float)th[0], fb = (float)th[1], ftg = (float)(tau * th[3]);
+  const float w_max = (float)pb.w_max;
+  const double h2inv = (double)N * N;
+  const int nfo = (S.field_mask & 1) + ((S.field_mask >> 1) & 1);
+  double phi = 0.0;
+  int bad = 0;
+  int next_obs = 0;
+  __syncthreads();
+  for (int step = 0; step < pb.n_steps; ++step) {
+    const double rho = exp(r * (double)step * tau);
+    const double rho2inv = 1.0 / (rho * rho);
+    const float alpha = (float)(1.0 + tau * 2.0 * r);  // m = 2 in 2-D
+    const float bu = (float)(tau * rho2inv * h2inv);
+    const float bv = (float)(tau * d * rho2inv * h2inv);
+    for (int i = tid; i < NPTS; i += kSimtThreads) {
+      const int y = i / N, x = i - y * N, o = y * NP + x;
+      const float uu = U[o], vv = V[o];
+      const float u2v = uu * uu * vv;
+      U[o] = fmaf(ftg, fa - uu + u2v, uu);
+      V[o] = fmaf(ftg, fb - u2v, vv);
+    }
+    __syncthreads();
+    implicit_solve_simt<N>(U, Cm, alpha, bu, mur, muc, ty, tx);
+    implicit_solve_simt<N>(V, Cm, alpha, bv, mur, muc, ty, tx);
+    if (next_obs < S.n_obs && step + 1 == S.obs_steps[next_obs]) {
+      const float* yo = S.yf + (size_t)next_obs * nfo * NPTS;
+      int fo = 0;
+      for (int f = 0; f < 2; ++f) {
+        if (!(S.field_mask & (1 << f))) continue;
+        const float* W = f ? V : U;
+        const float* yf = yo + (size_t)fo * NPTS;
+        for (int i = tid; i < NPTS; i += kSimtThreads) {
+          const int y = i / N, x = i - y * N;
+          const float w = W[y * NP + x];
+          if (!(fabsf(w) <= w_max)) bad = 1;  // also catches NaN
+          const double e = (double)(yf[i] - w);
+          phi += e * e;
+        }
+        ++fo;
+      }
+      ++next_obs;
+    }
+  }
+  const double tot = cta_sum(phi, red);
+  const int any_bad = __syncthreads_or(bad);
+  if (tid == 0) {
+    *st_out = any_bad ? (uint32_t)RD_P_NONFINITE : 0u;
+    *phi_out = any_bad ? (double)INFINITY : tot * S.inv_two_sigma2;
+  }
+  if (fields_out) {
+    for (int i = tid; i < NPTS; i += kSimtThreads) {
+      const int y = i / N, x = i - y * N;
+      fields_out[i] = U[y * NP + x];
+      fields_out[NPTS + i] = V[y * NP + x];
+    }
+  }
+  __syncthreads();
+}
+
+#define RD_SIMT_CASE(NN)                                                      \
+  case NN:                                                                    \
+    if constexpr (NN <= NMAX)                                                 \
+      solve2d_simt_item<NN>(pb, S, th, sm, red, &phi[b], &status[b], fo);     \
+    break;
+
+// NMAX: largest grid of the problem; sizes up to NMAX share one launch.
+template <int NMAX, int MINB>
+__global__ void __launch_bounds__(kSimtThreads, MINB)
+    k_solve2d_simt(DevProblem pb, WorkQueue q, const double* theta, double* phi,
+                   uint32_t* status, float* fields, size_t field_stride) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ double red[kSimtThreads / 32];
+  __shared__ int s_item, s_size;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int s = 0;
+      s_item = queue_pop(q, &s);
+      s_size = s;
+    }
+    __syncthreads();
+    const int b = s_item, s = s_size;
+    __syncthreads();
+    if (b < 0) break;
+    double th[5];
+    full_theta(pb, theta + (size_t)b * pb.n_params, th);
+    const DevSize& S = pb.sz[s];
+    float* fo = fields ? fields + (size_t)b * field_stride : nullptr;
+    switch (S.n) {
+      RD_SIMT_CASE(16)
+      RD_SIMT_CASE(32)
+      RD_SIMT_CASE(48)
+      RD_SIMT_CASE(64)
+      RD_SIMT_CASE(80)
+      RD_SIMT_CASE(96)
+      RD_SIMT_CASE(112)
+      RD_SIMT_CASE(128)
+      default:
+        break;
+    }
+  }
+}
+#undef RD_SIMT_CASE
+
+size_t simt2d_smem_bytes(int n) {
+  return (size_t)3 * n * (n + 1) * sizeof(float);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+__global__ void k_fill_queue(WorkQueue q, int B, const int* size_idx,
+                             double* phi, uint32_t* status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const int s = size_idx ? size_idx[b] : 0;
+  if (s < 0 || s >= q.n_sizes) {
+    phi[b] = (double)INFINITY;
+    status[b] = RD_P_OUT_OF_SUPPORT;
+    return;
+  }
+  const int i = atomicAdd(&q.counts[s], 1);
+  q.items[(size_t)s * q.capacity + i] = b;
+}
+
+cudaError_t launch_fill_queue(const WorkQueue& q, int B, const int* size_idx,
+                              double* phi, uint32_t* status, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(q.counts, 0, 2 * kMaxSizes * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (B > 0) k_fill_queue<<<(B + 255) / 256, 256, 0, st>>>(q, B, size_idx, phi, status);
+  return cudaGetLastError();
+}
+
+// Kernel variant for a problem whose largest grid is max_n: the 1-D bucket
+// (local arrays of 64 or 256 doubles) or the 2-D NMAX instantiation with the
+// CTAs-per-SM hint that its shared memory allows.
+template <typename F>
+static auto with_simt_kernel(int dim, int max_n, F&& f) {
+  if (dim == 1) {
+    if (max_n <= 64) return f((const void*)k_solve1d_f64<64>, 0);
+    return f((const void*)k_solve1d_f64<256>, 0);
+  }
+  if (max_n <= 32) return f((const void*)k_solve2d_simt<32, 4>, 32);
+  if (max_n <= 64) return f((const void*)k_solve2d_simt<64, 4>, 64);
+  if (max_n <= 96) return f((const void*)k_solve2d_simt<96, 2>, 96);
+  return f((const void*)k_solve2d_simt<128, 1>, 128);
+}
+
+cudaError_t launch_solve_simt(const DevProblem& pb, const WorkQueue& q,
+                              const double* theta, double* phi, uint32_t* status,
+                              void* fields, int grid, cudaStream_t st) {
+  const size_t stride = (size_t)2 * (pb.dim == 1 ? pb.max_n : pb.max_n * pb.max_n);
+  const double* th = theta;
+  void* fo = fields;
+  DevProblem pbv = pb;
+  WorkQueue qv = q;
+  size_t stride_v = stride;
+  return with_simt_kernel(pb.dim, pb.max_n, [&](const void* fn, int nmax) {
+    const size_t smem = pb.dim == 1 ? 0 : simt2d_smem_bytes(nmax);
+    const int threads = pb.dim == 1 ? 128 : kSimtThreads;
+    void* args[] = {&pbv, &qv, (void*)&th, &phi, &status, &fo, &stride_v};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st);
+  });
+}
+
+cudaError_t setup_solve_simt(int dim, int max_n) {
+  return with_simt_kernel(dim, max_n, [&](const void* fn, int nmax) {
+    if (dim == 1) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)simt2d_smem_bytes(nmax));
+  });
+}
+
+int grid_solve_simt(int dim, int max_n, int n_sm) {
+  return with_simt_kernel(dim, max_n, [&](const void* fn, int nmax) {
+    int per_sm = 0;
+    const size_t smem = dim == 1 ? 0 : simt2d_smem_bytes(nmax);
+    const int threads = dim == 1 ? 128 : kSimtThreads;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    return n_sm * per_sm;
+  });
+}
+
+}  // namespace rd

@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the
+same seeded inputs: forward fields, log-likelihoods, statuses and chains.
+
+Tolerances (north-star, written here): fields at T within relative L2 1e-4
+for the FP64 1-D workload and 1e-3 for FP32 2-D fields; the log-likelihood
+reduction within 1e-6 relative on identical fields; end-to-end FP32 Phi within
+the change that the field tolerance allows (gpu_helpers.phi_tolerance)."""
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1605_04718_gb300 as rd
+import rd_synth
+from oracle import mcmc
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1605_04718_gb300 import build
+    build.build()
+    oracle.build()
+    rd.load()
+
+
+def _eval(p, theta, size_idx=None, n=None, n_fields=2, dtype=torch.float32):
+    B = theta.shape[0]
+    th = torch.tensor(theta, dtype=torch.float64, device=DEV)
+    phi = torch.zeros(B, dtype=torch.float64, device=DEV)
+    st = torch.zeros(B, dtype=torch.int32, device=DEV)
+    sz = torch.tensor(size_idx, dtype=torch.int32, device=DEV) if size_idx is not None else None
+    fl = None
+    if n is not None:
+        fl = torch.full((B, n_fields) + n, float("nan"), dtype=dtype, device=DEV)
+    rd.rd_evaluate_batch(p, th, phi, st, size_idx=sz, fields=fl)
+    torch.cuda.synchronize()
+    return (phi.cpu().numpy(), st.cpu().numpy().astype(np.uint32),
+            None if fl is None else fl.double().cpu().numpy())
+
+
+def _prior_draws(n, seed):
+    return rd_synth.lognormal_draws([0.1, 0.9, 10.0, 200.0], [0.15] * 4, n, seed)
+
+
+# ------------------------------------------------------------------ 1-D FP64
+def _problem_1d(n_steps=None):
+    spec = rd_synth.DATASETS["rd1d_n64"]
+    ds = H.load_dataset("rd1d_n64")
+    n_steps = n_steps or spec["n_steps"]
+    desc = rd.make_desc(1, [64], spec["tau"], n_steps, [0, 1], [0.1, 0.9, 10.0, 200.0, 0.0],
+                        [rd.RD_PRIOR_UNIFORM] * 2, [0.0, 0.0], [1.0, 2.0], [rd.RD_STEP_LINEAR] * 2,
+                        solver=rd.RD_SOLVER_THOMAS)
+    p = rd.rd_problem_create(desc)
+    rd.rd_set_initial_state(p, 0, ds["u0"], ds["v0"])
+    steps = [n_steps]
+    rd.rd_set_observations(p, 0, steps, 1, ds["y"], spec["sigma"])
+    P = oracle.Problem(1, 64, spec["tau"], n_steps, ds["u0"], ds["v0"], y=ds["y"],
+                       obs_steps=steps, field_mask=1, sigma=spec["sigma"])
+    return p, P
+
+
+def test_1d_fp64_fields_and_phi_match_oracle():
+    p, P = _problem_1d()
+    theta = np.array([[0.1, 0.9], [0.11, 0.88], [0.095, 0.93], [0.3, 1.5], [0.05, 0.2]])
+    phi, st, fl = _eval(p, theta, n=(64,), dtype=torch.float64)
+    for i in range(len(theta)):
+        po, so, uo, vo = P.forward([theta[i, 0], theta[i, 1], 10.0, 200.0, 0.0])
+        assert st[i] == so == 0
+        assert H.rel_l2(fl[i, 0], uo) < 1e-4 and H.rel_l2(fl[i, 1], vo) < 1e-4
+        assert H.rel_l2(fl[i, 0], uo) < 1e-10  # FP64 on both sides
+        assert abs(phi[i] - po) <= 1e-6 * abs(po)
+    rd.rd_problem_destroy(p)
+
+
+def test_1d_chains_match_oracle_trajectories():
+    """4 chains x 500 steps of the 1-D workload (uniform prior [0,1] x [0,2],
+    step 0.01): same seed, same Philox streams, FP64 on both sides -> the
+    same accept decisions and the same samples."""
+    p, P = _problem_1d()
+    C, S = 4, 500
+    theta0 = rd_synth.chain_starts([0.1, 0.9], C, seed=100)
+    c = rd.rd_chains_create(p, theta0, 1234, [0.01, 0.01], capacity=S)
+    rd.rd_chains_run(c, S)
+    s_gpu, counters = rd.rd_chains_read_samples(c, S, 2, C)
+    m = mcmc.Model([0, 1], np.array([0.1, 0.9, 10.0, 200.0, 0.0]), ["uniform"] * 2,
+                   np.array([0.0, 0.0]), np.array([1.0, 2.0]), ["linear"] * 2,
+                   np.array([0.01, 0.01]))
+    ch = mcmc.Chains(m, theta0, 1234, lambda th: P.forward_batch(th))
+    s_orc = ch.run(S)
+    assert np.allclose(s_gpu, s_orc, rtol=1e-9, atol=1e-12)
+    assert counters[0] == C * S and counters[2] == ch.n_acc
+    rd.rd_chains_destroy(c)
+    rd.rd_problem_destroy(p)
+
+
+# ------------------------------------------------------------------ 2-D FP32
+@pytest.mark.parametrize("n,n_steps", [(16, 400), (32, 400), (48, 300), (64, 200)])
+def test_2d_fields_and_phi_match_oracle(n, n_steps):
+    ds = H.small_dataset(n, n_steps, seed=n)
+    p = H.gpu_problem([ds])
+    theta = np.concatenate([[[0.1, 0.9, 10.0, 200.0]], _prior_draws(23, seed=n)])
+    phi, st, fl = _eval(p, theta, n=(n, n))
+    P = H.oracle_problem(ds)
+    res = P.forward_batch(np.concatenate([theta, np.zeros((len(theta), 1))], 1),
+                          want_fields=True)
+    for i in range(len(theta)):
+        po, so, fo = res[0][i], res[1][i], res[2][i]
+        assert st[i] == so
+        if so:
+            continue
+        w_o = fo.reshape(2, -1)
+        w_g = fl[i].reshape(2, -1)
+        assert H.rel_l2(w_g, w_o) < 1e-3, (i, H.rel_l2(w_g, w_o))
+        tol = H.phi_tolerance(ds["y"].reshape(2, -1), w_o, ds["sigma"])
+        assert abs(phi[i] - po) <= tol, (i, phi[i], po, tol)
+        # the log-likelihood reduction on the GPU's own fields, FP64 definition
+        ref = ((ds["y"].reshape(2, -1).astype(np.float32) - w_g.astype(np.float32))
+               .astype(np.float64) ** 2).sum() / (2 * ds["sigma"] ** 2)
+        assert abs(phi[i] - ref) <= 1e-6 * ref
+    rd.rd_problem_destroy(p)
+
+
+def test_mixed_sizes_in_one_launch():
+    dss = [H.small_dataset(n, 200, seed=100 + n) for n in (48, 16, 32)]
+    p = H.gpu_problem(dss)
+    B = 30
+    theta = _prior_draws(B, seed=5)
+    size_idx = np.arange(B) % 3
+    phi, st, fl = _eval(p, theta, size_idx=size_idx, n=(48, 48))
+    for s, ds in enumerate(dss):
+        n = ds["n"]
+        P = H.oracle_problem(ds)
+        idx = np.nonzero(size_idx == s)[0]
+        res = P.forward_batch(np.concatenate([theta[idx], np.zeros((len(idx), 1))], 1),
+                              want_fields=True)
+        for k, i in enumerate(idx):
+            assert st[i] == res[1][k]
+            w_g = fl[i].reshape(-1)[: 2 * n * n].reshape(2, n, n)
+            assert H.rel_l2(w_g, res[2][k]) < 1e-3
+            assert abs(phi[i] - res[0][k]) <= H.phi_tolerance(
+                ds["y"].reshape(2, -1), res[2][k].reshape(2, -1), ds["sigma"])
+    rd.rd_problem_destroy(p)
+
+
+def test_edge_cases_empty_nonfinite_bad_size():
+    ds = H.small_dataset(16, 100, seed=3)
+    p = H.gpu_problem([ds])
+    rd.rd_evaluate_batch(p, torch.zeros((0, 4), dtype=torch.float64, device=DEV),
+                         torch.zeros(0, dtype=torch.float64, device=DEV),
+                         torch.zeros(0, dtype=torch.int32, device=DEV))
+    theta = np.array([[0.1, 0.9, 10.0, 200.0], [0.1, 0.9, 10.0, 5e4], [0.1, 0.9, 10.0, 200.0]])
+    phi, st, _ = _eval(p, theta, size_idx=[0, 0, 3])
+    assert st[0] == 0 and np.isfinite(phi[0])
+    assert st[1] & rd.RD_P_NONFINITE and np.isinf(phi[1])
+    assert st[2] == rd.RD_P_OUT_OF_SUPPORT and np.isinf(phi[2])
+    P = H.oracle_problem(ds)
+    po, so, _, _ = P.forward([0.1, 0.9, 10.0, 5e4, 0.0])
+    assert so & oracle.ST_NONFINITE
+    rd.rd_problem_destroy(p)
+
+
+def _oracle_sampled(P, theta_rows):
+    with cf.ThreadPoolExecutor(max_workers=len(theta_rows)) as ex:
+        return list(ex.map(lambda t: P.forward(list(t) + [0.0]), theta_rows))
+
+
+@pytest.mark.parametrize("name,B", [("rd2d_n64", 2048), ("rd2d_n128", 1024)])
+def test_full_size_sampled_outputs(name, B):
+    """Full 8000-step solves in the benchmark's launch configuration (one
+    persistent launch over B proposals); three sampled proposals are checked
+    against the oracle one by one."""
+    ds = H.stored_2d(name)
+    n = ds["n"]
+    p = H.gpu_problem([ds])
+    theta = _prior_draws(B, seed=77)
+    theta[0] = [0.1, 0.9, 10.0, 200.0]
+    phi, st, fl = _eval(p, theta, n=(n, n))
+    pick = [0, B // 2 + 1, B - 1]
+    P = H.oracle_problem(ds)
+    outs = _oracle_sampled(P, theta[pick])
+    for i, (po, so, uo, vo) in zip(pick, outs):
+        assert st[i] == so
+        if so:
+            continue
+        w_o = np.stack([uo, vo])
+        assert H.rel_l2(fl[i], w_o) < 1e-3
+        assert abs(phi[i] - po) <= H.phi_tolerance(ds["y"].reshape(2, -1),
+                                                   w_o.reshape(2, -1), ds["sigma"])
+    ok = st == 0
+    assert ok.mean() > 0.9 and np.all(np.isfinite(phi[ok]))
+    rd.rd_problem_destroy(p)
+
+
+# ------------------------------------------------------------------ chains
+def _model4(step):
+    return mcmc.Model([0, 1, 2, 3], np.array([0.1, 0.9, 10.0, 200.0, 0.0]), ["lognormal"] * 4,
+                      np.array([0.1, 0.9, 10.0, 200.0]), np.array([0.5] * 4), ["log"] * 4,
+                      np.asarray(step))
+
+
+def test_2d_chains_posterior_matches_oracle():
+    """Small 2-D posterior (16^2, 100 steps, sigma 0.05): 64 chains x 400
+    steps on both sides; posterior means and 95% interval ends agree within
+    3 Monte Carlo standard errors, and most early decisions coincide."""
+    ds = H.small_dataset(16, 100, seed=9, sigma=0.05)
+    p = H.gpu_problem([ds])
+    C, S = 64, 400
+    step = [0.02, 0.02, 0.05, 0.05]
+    theta0 = rd_synth.chain_starts([0.1, 0.9, 10.0, 200.0], C, seed=200)
+    c = rd.rd_chains_create(p, theta0, 99, step, capacity=S)
+    rd.rd_chains_run(c, S)
+    s_gpu, _ = rd.rd_chains_read_samples(c, S, 4, C)
+    P = H.oracle_problem(ds)
+    ch = mcmc.Chains(_model4(step), theta0, 99, lambda th: P.forward_batch(th))
+    s_orc = ch.run(S)
+    same_first = np.mean(np.all(np.isclose(s_gpu[:20], s_orc[:20], rtol=1e-6), axis=(0, 1)))
+    assert same_first > 0.8
+    burn = S // 4
+    for j in range(4):
+        g = s_gpu[burn:, j, :]
+        o = s_orc[burn:, j, :]
+        ess = min(sum(mcmc.ess_plain(g[:, k]) for k in range(C)),
+                  sum(mcmc.ess_plain(o[:, k]) for k in range(C)))
+        sd = o.std()
+        mcse = sd * np.sqrt(2.0 / ess)
+        assert abs(g.mean() - o.mean()) < 3 * mcse + 1e-12, (j, g.mean(), o.mean(), mcse)
+        for q in (0.025, 0.975):
+            assert abs(np.quantile(g, q) - np.quantile(o, q)) < 3 * 1.5 * mcse + 1e-12
+    rd.rd_chains_destroy(c)
+    rd.rd_problem_destroy(p)
+
+
+def test_chains_checkpoint_restore_is_bit_identical():
+    ds = H.small_dataset(16, 50, seed=4)
+    p = H.gpu_problem([ds])
+    C = 16
+    theta0 = rd_synth.chain_starts([0.1, 0.9, 10.0, 200.0], C, seed=3)
+    step = [0.02] * 4
+    c1 = rd.rd_chains_create(p, theta0, 5, step, capacity=64)
+    rd.rd_chains_run(c1, 10)
+    blob = rd.rd_chains_checkpoint(c1)
+    rd.rd_chains_read_samples(c1, 64, 4, C)
+    rd.rd_chains_run(c1, 12)
+    a, ca = rd.rd_chains_read_samples(c1, 64, 4, C)
+    c2 = rd.rd_chains_create(p, theta0 * 1.5, 5, step, capacity=64)
+    rd.rd_chains_restore(c2, blob)
+    rd.rd_chains_run(c2, 12)
+    b, cb = rd.rd_chains_read_samples(c2, 64, 4, C)
+    assert np.array_equal(a, b) and np.array_equal(ca, cb)
+    # a partial read returns the oldest samples first and keeps the rest
+    rd.rd_chains_run(c2, 5)
+    first, _ = rd.rd_chains_read_samples(c2, 2, 4, C)
+    rest, _ = rd.rd_chains_read_samples(c2, 64, 4, C)
+    assert first.shape[0] == 2 and rest.shape[0] == 3
+    th, _ = rd.rd_chains_get_state(c2, 4, C)
+    assert np.array_equal(rest[-1].T, th)
+    for c in (c1, c2):
+        rd.rd_chains_destroy(c)
+    rd.rd_problem_destroy(p)
