@@ -249,6 +249,15 @@ rd_status rd_set_initial_state(rd_problem* p, int size_idx, const double* u0,
     S.u0d = d;
     S.v0d = d + npts;
   } else {
+    // FP32 fields are stored as deviations from the spatial mean of the
+    // initial state (see the 2-D solve kernel)
+    double mu_u = 0.0, mu_v = 0.0;
+    for (size_t i = 0; i < npts; ++i) {
+      mu_u += u0[i];
+      mu_v += v0[i];
+    }
+    S.ref_u = (float)(mu_u / (double)npts);
+    S.ref_v = (float)(mu_v / (double)npts);
     std::vector<float> h(2 * npts);
     for (size_t i = 0; i < npts; ++i) {
       h[i] = (float)u0[i];

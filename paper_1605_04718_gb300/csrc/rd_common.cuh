@@ -28,6 +28,7 @@ struct DevSize {
   const double* v0d;
   const float* yf;          // FP32 observations [n_obs][fields][npts] (2-D)
   const double* yd;         // FP64 observations (1-D)
+  float ref_u, ref_v;       // reference state: spatial mean of the initial state
   const float* cmat;        // orthonormal DCT-II matrix C[k][i], FP32 [n][n]
   const float* mu;          // 4 sin^2(pi k / (2n)), FP32 [n]
 };

@@ -25,57 +25,68 @@ namespace rd {
 // Neumann matrix (diagonal alpha + 2 beta, alpha + beta in the two boundary
 // rows, off-diagonals -beta).
 // ---------------------------------------------------------------------------
+// Factors of the Thomas elimination for [alpha I - beta Lap_h]: inverse
+// pivots inv[i] and modified super-diagonal cp[i] = -beta inv[i].
+template <int NMAX>
+__device__ __forceinline__ void thomas_factors(int n, double alpha, double beta,
+                                               double (&cp)[NMAX], double (&inv)[NMAX]) {
+  double prev = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double diag = alpha + ((i == 0 || i == n - 1) ? beta : 2.0 * beta);
+    const double den = diag + beta * prev;
+    inv[i] = 1.0 / den;
+    cp[i] = -beta * inv[i];
+    prev = cp[i];
+  }
+}
+
 template <int NMAX>
 __device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
                              const double th[5], double* phi_out,
                              uint32_t* st_out, double* fields_out) {
-  double u[NMAX], v[NMAX], ru[NMAX], rv[NMAX], cu[NMAX], cv[NMAX];
+  double u[NMAX], v[NMAX], ru[NMAX], rv[NMAX];
+  double cu[NMAX], cv[NMAX], iu[NMAX], iv[NMAX];
   const int n = S.n;
   for (int i = 0; i < n; ++i) {
     u[i] = S.u0d[i];
     v[i] = S.v0d[i];
   }
   const double a = th[0], b = th[1], d = th[2], g = th[3], r = th[4];
-  const double tau = pb.tau, h2inv = (double)n * n;
+  const double tau = pb.tau, h2inv = (double)n * n, tg = tau * g;
   const int nfo = (S.field_mask & 1) + ((S.field_mask >> 1) & 1);
+  const bool grow = (r != 0.0);
   double phi = 0.0;
   bool bad = false;
   int next_obs = 0;
+  double alpha = 1.0, bu = tau * h2inv, bv = tau * d * h2inv;
+  thomas_factors<NMAX>(n, alpha, bu, cu, iu);
+  thomas_factors<NMAX>(n, alpha, bv, cv, iv);
   for (int step = 0; step < pb.n_steps; ++step) {
-    const double rho = exp(r * (double)step * tau);
-    const double alpha = 1.0 + tau * 1.0 * r;  // m = 1 in 1-D
-    const double bu = tau / (rho * rho) * h2inv;
-    const double bv = tau * d / (rho * rho) * h2inv;
+    if (grow) {  // rho_n = exp(r t_n): the matrix changes every step
+      const double rho = exp(r * (double)step * tau);
+      alpha = 1.0 + tau * 1.0 * r;  // m = 1 in 1-D
+      bu = tau / (rho * rho) * h2inv;
+      bv = tau * d / (rho * rho) * h2inv;
+      thomas_factors<NMAX>(n, alpha, bu, cu, iu);
+      thomas_factors<NMAX>(n, alpha, bv, cv, iv);
+    }
+    // explicit reaction fused with the forward elimination
+    double pu = 0.0, pv = 0.0;
     for (int i = 0; i < n; ++i) {
       const double uu = u[i], vv = v[i];
       const double u2v = uu * uu * vv;
-      ru[i] = uu + tau * g * (a - uu + u2v);
-      rv[i] = vv + tau * g * (b - u2v);
+      const double rU = uu + tg * (a - uu + u2v);
+      const double rV = vv + tg * (b - u2v);
+      pu = (rU + bu * pu) * iu[i];
+      pv = (rV + bv * pv) * iv[i];
+      ru[i] = pu;
+      rv[i] = pv;
     }
-    if (n == 1) {
-      u[0] = ru[0] / alpha;
-      v[0] = rv[0] / alpha;
-    } else {
-      // forward elimination (cu, cv: modified super-diagonal; ru, rv: rhs)
-      double den_u = alpha + bu, den_v = alpha + bv;
-      cu[0] = -bu / den_u;
-      cv[0] = -bv / den_v;
-      ru[0] /= den_u;
-      rv[0] /= den_v;
-      for (int i = 1; i < n; ++i) {
-        const double du = (i == n - 1 ? alpha + bu : alpha + 2.0 * bu) + bu * cu[i - 1];
-        const double dv = (i == n - 1 ? alpha + bv : alpha + 2.0 * bv) + bv * cv[i - 1];
-        cu[i] = -bu / du;
-        cv[i] = -bv / dv;
-        ru[i] = (ru[i] + bu * ru[i - 1]) / du;
-        rv[i] = (rv[i] + bv * rv[i - 1]) / dv;
-      }
-      u[n - 1] = ru[n - 1];
-      v[n - 1] = rv[n - 1];
-      for (int i = n - 2; i >= 0; --i) {
-        u[i] = ru[i] - cu[i] * u[i + 1];
-        v[i] = rv[i] - cv[i] * v[i + 1];
-      }
+    u[n - 1] = ru[n - 1];
+    v[n - 1] = rv[n - 1];
+    for (int i = n - 2; i >= 0; --i) {
+      u[i] = ru[i] - cu[i] * u[i + 1];
+      v[i] = rv[i] - cv[i] * v[i + 1];
     }
     if (next_obs < S.n_obs && step + 1 == S.obs_steps[next_obs]) {
       const double* yo = S.yd + (size_t)next_obs * nfo * n;
@@ -121,6 +132,14 @@ __global__ void k_solve1d_f64(DevProblem pb, WorkQueue q, const double* theta,
 // ---------------------------------------------------------------------------
 // 2-D, FP32 fields, one CTA of 256 threads per proposal with u, v and the DCT
 // matrix resident in shared memory for the whole time loop.
+//
+// The fields are held as deviations du = u - u_ref, dv = v - v_ref from the
+// spatial mean of the initial state.  The solve is linear and constants are
+// in the kernel of the Laplacian, so the step for the deviations is
+//   [alpha I - beta Lap_h] dw^{n+1} = dw^n + tau gamma kin(u, v) + (1 - alpha) w_ref,
+// the same step as for w.  FP32 rounding then acts on |dw| (about 0.01 while
+// a Turing pattern grows from the initial noise) instead of on |w| ~ 1,
+// which keeps the small unstable modes accurate.
 //
 // Implicit solve by diagonalisation in the Neumann eigenbasis (orthonormal
 // DCT-II, C[k][i] = c_k cos(pi k (i + 1/2) / N)):
@@ -228,15 +247,16 @@ __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
                                   double* phi_out, uint32_t* st_out,
                                   float* fields_out) {
   constexpr int TM = N / 16, NP = N + 1, NPTS = N * N;
-  float* U = sm;
-  float* V = sm + N * NP;
+  float* U = sm;  // u - ref_u
+  float* V = sm + N * NP;  // v - ref_v
   float* Cm = sm + 2 * N * NP;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const float ref_u = S.ref_u, ref_v = S.ref_v;
   for (int i = tid; i < NPTS; i += kSimtThreads) {
     const int r = i / N, c = i - r * N;
     Cm[r * NP + c] = S.cmat[i];
-    U[r * NP + c] = S.u0f[i];
-    V[r * NP + c] = S.v0f[i];
+    U[r * NP + c] = S.u0f[i] - ref_u;
+    V[r * NP + c] = S.v0f[i] - ref_v;
   }
   float mur[TM], muc[TM];
 #pragma unroll
@@ -259,12 +279,15 @@ __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
     const float alpha = (float)(1.0 + tau * 2.0 * r);  // m = 2 in 2-D
     const float bu = (float)(tau * rho2inv * h2inv);
     const float bv = (float)(tau * d * rho2inv * h2inv);
+    const float cu = (float)(-tau * 2.0 * r * (double)ref_u);  // (1 - alpha) ref
+    const float cv = (float)(-tau * 2.0 * r * (double)ref_v);
     for (int i = tid; i < NPTS; i += kSimtThreads) {
       const int y = i / N, x = i - y * N, o = y * NP + x;
-      const float uu = U[o], vv = V[o];
+      const float du = U[o], dv = V[o];
+      const float uu = ref_u + du, vv = ref_v + dv;
       const float u2v = uu * uu * vv;
-      U[o] = fmaf(ftg, fa - uu + u2v, uu);
-      V[o] = fmaf(ftg, fb - u2v, vv);
+      U[o] = fmaf(ftg, fa - uu + u2v, du) + cu;
+      V[o] = fmaf(ftg, fb - u2v, dv) + cv;
     }
     __syncthreads();
     implicit_solve_simt<N>(U, Cm, alpha, bu, mur, muc, ty, tx);
@@ -275,12 +298,13 @@ __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
       for (int f = 0; f < 2; ++f) {
         if (!(S.field_mask & (1 << f))) continue;
         const float* W = f ? V : U;
+        const double ref = f ? (double)ref_v : (double)ref_u;
         const float* yf = yo + (size_t)fo * NPTS;
         for (int i = tid; i < NPTS; i += kSimtThreads) {
           const int y = i / N, x = i - y * N;
-          const float w = W[y * NP + x];
-          if (!(fabsf(w) <= w_max)) bad = 1;  // also catches NaN
-          const double e = (double)(yf[i] - w);
+          const double w = ref + (double)W[y * NP + x];
+          if (!(fabs(w) <= (double)w_max)) bad = 1;  // also catches NaN
+          const double e = (double)yf[i] - w;
           phi += e * e;
         }
         ++fo;
@@ -297,8 +321,8 @@ __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
   if (fields_out) {
     for (int i = tid; i < NPTS; i += kSimtThreads) {
       const int y = i / N, x = i - y * N;
-      fields_out[i] = U[y * NP + x];
-      fields_out[NPTS + i] = V[y * NP + x];
+      fields_out[i] = ref_u + U[y * NP + x];
+      fields_out[NPTS + i] = ref_v + V[y * NP + x];
     }
   }
   __syncthreads();
