@@ -48,8 +48,18 @@ WorkQueue make_queue(const rd_problem* p) {
   return q;
 }
 
+bool uses_tc(const rd_problem* p) {
+  return p->desc.dim == 2 &&
+         (p->desc.solver == RD_SOLVER_DCT_TC || p->desc.solver == RD_SOLVER_AUTO);
+}
+
 cudaError_t launch_solve_on(rd_problem* p, const double* theta, double* phi,
                             uint32_t* status, void* fields, cudaStream_t st) {
+  if (uses_tc(p)) {
+    const int grid = grid_solve_tc(p->dev.max_n, p->n_sm);
+    return launch_solve_tc(p->dev, make_queue(p), theta, phi, status, fields, grid,
+                           p->ws.err, st);
+  }
   const int grid = grid_solve_simt(p->desc.dim, p->dev.max_n, p->n_sm);
   return launch_solve_simt(p->dev, make_queue(p), theta, phi, status, fields,
                            grid, st);
@@ -189,7 +199,9 @@ rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
     }
   }
   if (cudaMalloc(&p->ws.queue_counters, sizeof(int) * 2 * kMaxSizes) != cudaSuccess ||
-      cudaMemset(p->ws.queue_counters, 0, sizeof(int) * 2 * kMaxSizes) != cudaSuccess) {
+      cudaMemset(p->ws.queue_counters, 0, sizeof(int) * 2 * kMaxSizes) != cudaSuccess ||
+      cudaMalloc(&p->ws.err, sizeof(int)) != cudaSuccess ||
+      cudaMemset(p->ws.err, 0, sizeof(int)) != cudaSuccess) {
     rd_problem_destroy(p);
     set_error("device allocation of the work queue failed");
     return RD_ENOMEM;
@@ -198,9 +210,10 @@ rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
     rd_problem_destroy(p);
     return RD_ENOMEM;
   }
-  if (setup_solve_simt(desc->dim, dv.max_n) != cudaSuccess) {
+  if (setup_solve_simt(desc->dim, dv.max_n) != cudaSuccess ||
+      (uses_tc(p) && setup_solve_tc(dv.max_n) != cudaSuccess)) {
     rd_problem_destroy(p);
-    set_error("cannot configure the 2-D solve kernel's shared memory");
+    set_error("cannot configure the solve kernels' shared memory");
     return RD_ECUDA;
   }
   *out = p;
@@ -218,6 +231,7 @@ rd_status rd_problem_destroy(rd_problem* p) {
   }
   cudaFree(p->ws.queue_items);
   cudaFree(p->ws.queue_counters);
+  cudaFree(p->ws.err);
   cudaFree(p->h2d_theta);
   cudaFree(p->h2d_size);
   cudaFree(p->d2h_phi);
@@ -380,6 +394,13 @@ rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
 rd_status rd_sync(rd_problem* p) {
   RD_CHECK(p, RD_EINVAL, "problem is NULL");
   RD_CUDA(cudaStreamSynchronize(p->stream));
+  int err = 0;
+  RD_CUDA(cudaMemcpy(&err, p->ws.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    RD_CUDA(cudaMemset(p->ws.err, 0, sizeof(int)));
+    set_error("a solve kernel's bounded wait gave up; its results are invalid");
+    return RD_ETIMEOUT;
+  }
   return RD_OK;
 }
 

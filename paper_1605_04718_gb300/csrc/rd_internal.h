@@ -20,6 +20,7 @@ void set_error(const std::string& msg);
 struct Workspace {
   int* queue_items = nullptr;   // [n_sizes][capacity]
   int* queue_counters = nullptr;  // [2 * kMaxSizes]: counts, pops
+  int* err = nullptr;             // set by a kernel whose bounded wait gave up
   int capacity = 0;
 };
 
@@ -86,6 +87,13 @@ cudaError_t launch_solve_simt(const DevProblem& pb, const WorkQueue& q,
                               const double* theta, double* phi, uint32_t* status,
                               void* fields, int grid, cudaStream_t st);
 cudaError_t setup_solve_simt(int dim, int max_n);
+cudaError_t setup_solve_tc(int max_n);
+int grid_solve_tc(int max_n, int n_sm);
+cudaError_t launch_solve_tc(const DevProblem& pb, const WorkQueue& q, const double* theta,
+                            double* phi, uint32_t* status, void* fields, int grid, int* err,
+                            cudaStream_t st);
+size_t tc_smem_bytes_host(int max_n);
+bool uses_tc(const rd_problem* p);
 int grid_solve_simt(int dim, int max_n, int n_sm);
 size_t simt2d_smem_bytes(int n);
 
