@@ -77,6 +77,7 @@ enum { RD_PREC_F64 = 0, RD_PREC_F32 = 1 };
 #define RD_MAX_SIZES 4
 #define RD_MAX_OBS 8
 #define RD_NPARAM 5
+#define RD_NOALLOC_MAX_BATCH 65536
 
 /*
  * Problem description.  Grid: cell-centred, x_i = (i + 1/2)/N, h = 1/N, in
@@ -143,6 +144,25 @@ rd_status rd_evaluate_batch(rd_problem* p, int B, const double* theta,
 rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
                                  const int* size_idx, double* loglik,
                                  uint32_t* status);
+
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory while they run -- e.g. a host whose device memory is
+ * all reserved by another allocator, or a time-critical loop that must not
+ * stall on the device-wide synchronisation of cudaFree -- because
+ * rd_evaluate_batch may grow the problem's workspace (cudaFree + cudaMalloc)
+ * when it sees a larger batch than before.
+ * Same arguments, results and stream behaviour as rd_evaluate_batch, but the
+ * call allocates nothing: the solve kernels' work lists live in one fixed
+ * device array of the library (about 1 MiB, held on every GPU that loads the
+ * library until the process exits), so B may be at most RD_NOALLOC_MAX_BATCH
+ * (EINVAL beyond).  The problem's device must be current.  The first call on
+ * a device also looks up that array's device address (no allocation); make
+ * that first call before any stream capture.  All calls share the array and
+ * each clears its counters before use, so calls whose GPU work overlaps (for
+ * example on two streams at once) race and must be serialised by the caller. */
+rd_status rd_evaluate_batch_noalloc(rd_problem* p, int B, const double* theta,
+                                    const int* size_idx, double* loglik,
+                                    uint32_t* status, void* fields);
 
 /* Chains: n_chains independent random-walk Metropolis chains advanced in
  * lock-step, one proposal per chain per step (Algorithm 1).

@@ -27,12 +27,13 @@ RD_PRIOR_UNIFORM, RD_PRIOR_LOGNORMAL = 0, 1
 RD_STEP_LINEAR, RD_STEP_LOG = 0, 1
 RD_PREC_F64, RD_PREC_F32 = 0, 1
 RD_MAX_SIZES, RD_MAX_OBS, RD_NPARAM = 4, 8, 5
+RD_NOALLOC_MAX_BATCH = 65536
 
 # Every entry point declared in include/rdbayes.h.
 EXPORTS = (
     "rd_problem_create", "rd_problem_destroy", "rd_set_stream",
     "rd_set_initial_state", "rd_set_observations", "rd_evaluate_batch",
-    "rd_evaluate_batch_host", "rd_chains_create", "rd_chains_destroy",
+    "rd_evaluate_batch_host", "rd_evaluate_batch_noalloc", "rd_chains_create", "rd_chains_destroy",
     "rd_chains_run", "rd_chains_read_samples", "rd_chains_get_state",
     "rd_chains_checkpoint", "rd_chains_restore", "rd_sync", "rd_last_error",
 )
@@ -80,6 +81,7 @@ def load():
     L.rd_set_observations.argtypes = [vp, i, i, vp, i, vp, d]
     L.rd_evaluate_batch.argtypes = [vp, i, vp, vp, vp, vp, vp]
     L.rd_evaluate_batch_host.argtypes = [vp, i, vp, vp, vp, vp]
+    L.rd_evaluate_batch_noalloc.argtypes = [vp, i, vp, vp, vp, vp, vp]
     L.rd_chains_create.argtypes = [vp, i, vp, ctypes.c_uint64, vp, vp, i, ctypes.POINTER(vp)]
     L.rd_chains_destroy.argtypes = [vp]
     L.rd_chains_run.argtypes = [vp, i]
@@ -182,6 +184,15 @@ def rd_evaluate_batch(p, theta, loglik, status, size_idx=None, fields=None):
     pattern of uint32), size_idx [B] int32 or None, fields or None: CUDA tensors."""
     _check(load().rd_evaluate_batch(p, theta.shape[0], _dev_ptr(theta), _dev_ptr(size_idx),
                                     _dev_ptr(loglik), _dev_ptr(status), _dev_ptr(fields)))
+
+
+def rd_evaluate_batch_noalloc(p, theta, loglik, status, size_idx=None, fields=None):
+    """As rd_evaluate_batch, for callers that cannot allocate device memory
+    during the call: the work lists use the library's fixed device array, so
+    B is limited to RD_NOALLOC_MAX_BATCH and overlapping calls must be
+    serialised by the caller (see include/rdbayes.h)."""
+    _check(load().rd_evaluate_batch_noalloc(p, theta.shape[0], _dev_ptr(theta), _dev_ptr(size_idx),
+                                            _dev_ptr(loglik), _dev_ptr(status), _dev_ptr(fields)))
 
 
 def rd_evaluate_batch_host(p, theta, size_idx=None):
