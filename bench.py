@@ -266,7 +266,7 @@ def run_gpu(args):
         flop_per_solve = 16.0 * n**3 * spec["n_steps"]  # 4 transforms x 2 N^3 x 2 fields / step
         bytes_per_solve = 16.0 * n * n * spec["n_steps"]  # u, v FP32 read + write per step
         clk = ck.get("sm_mhz") or 1900.0
-        if solver in (rd.RD_SOLVER_DCT_SIMT, rd.RD_SOLVER_AUTO):
+        if solver == rd.RD_SOLVER_DCT_SIMT:
             achieved = flop_per_solve * C / k_dur / 1e12
             fp32_peak = 152 * 128 * 2 * (ck.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
