@@ -78,6 +78,7 @@ enum { RD_PREC_F64 = 0, RD_PREC_F32 = 1 };
 #define RD_MAX_OBS 8
 #define RD_NPARAM 5
 #define RD_NOALLOC_MAX_BATCH 65536
+#define RD_SURROGATE_WIDTH 256
 
 /*
  * Problem description.  Grid: cell-centred, x_i = (i + 1/2)/N, h = 1/N, in
@@ -199,6 +200,69 @@ rd_status rd_chains_get_state(rd_chains* c, double* theta, double* phi);
  * problem, C and seed continues the chains bit-identically. */
 rd_status rd_chains_checkpoint(rd_chains* c, void* buf, size_t cap, size_t* n);
 rd_status rd_chains_restore(rd_chains* c, const void* buf, size_t n);
+
+/*
+ * Learned surrogate for delayed-acceptance sampling (not in the paper; the
+ * two-stage acceptance of Christen & Fox 2005, which keeps the posterior
+ * exact for any surrogate).  Network: x -> SiLU(W1 x + b1) -> SiLU(W2 . + b2)
+ * -> SiLU(W3 . + b3) -> W4 . + b4, width RD_SURROGATE_WIDTH, inputs
+ * x_j = (log theta_j - mu_j) / s_j for the n_params inferred parameters
+ * (padded to 16), output Phi~ = floor + exp(shift + scale * net).  BF16
+ * weights and activations, FP32 accumulation on the tensor cores, FP32 master
+ * weights.  Parameters (FP32, host order): W1 [W][16], b1 [W], W2 [W][W], b2,
+ * W3 [W][W], b3, W4 [W], b4 [1].  Normalisation vector (13 doubles):
+ * mu[5], s[5], floor, shift, scale.
+ */
+typedef struct {
+  int epochs;          /* passes over the training pairs (>= 1) */
+  int batch;           /* minibatch rows, a positive multiple of 128 */
+  double lr, beta1, beta2, weight_decay;  /* Adam with decoupled weight decay */
+  double holdout_frac; /* fraction of pairs held out for the error report */
+  uint64_t seed;       /* shuffling */
+} rd_train_desc;
+
+/* Creates a surrogate for problem p with seeded He-uniform initial weights. */
+rd_status rd_surrogate_create(rd_problem* p, uint64_t seed, rd_surrogate** out);
+rd_status rd_surrogate_destroy(rd_surrogate* s);
+
+/* Trains on n pairs (device theta [n][n_params], device Phi [n]; pairs with
+ * non-finite Phi are skipped): sets the normalisation from the data (inputs:
+ * mean/sd of log theta; targets: z = log(Phi - floor), floor = min Phi - 1,
+ * standardised), then minimises the mean squared error on z with Adam.
+ * report (host, may be NULL) [4]: final-epoch training MSE, hold-out MSE,
+ * hold-out mean relative |Phi~ - Phi| / Phi, wall seconds.  Synchronous. */
+rd_status rd_surrogate_train(rd_surrogate* s, int n, const double* theta,
+                             const double* phi, const rd_train_desc* td,
+                             double* report);
+
+/* Phi~ for B parameter vectors (device theta [B][n_params], device out [B]);
+ * async on the problem's stream. */
+rd_status rd_surrogate_predict(rd_surrogate* s, int B, const double* theta,
+                               double* phi_tilde);
+
+/* Mean squared error of the network output against normalised targets
+ * (device float [B]) for B rows of theta (B a multiple of 128), and its
+ * gradient with respect to every parameter (device float, parameter order;
+ * may be NULL).  *loss is written on the host.  Synchronous. */
+rd_status rd_surrogate_loss_grad(rd_surrogate* s, int B, const double* theta,
+                                 const float* target, double* loss,
+                                 float* grads);
+
+/* Parameters (host FP32, *n = count; buf may be NULL to query) and the
+ * normalisation (host, 13 doubles; may be NULL). */
+rd_status rd_surrogate_get_params(rd_surrogate* s, float* buf, size_t cap,
+                                  size_t* n, double* norm);
+rd_status rd_surrogate_set_params(rd_surrogate* s, const float* buf, size_t n,
+                                  const double* norm);
+
+/* Switches chains to delayed acceptance with surrogate s (NULL: back to plain
+ * Metropolis).  Each step then draws the proposal, evaluates Phi~ for every
+ * chain, accepts to stage 2 with probability
+ * min(1, exp(-Phi~(x_bar) + log mu0(x_bar) + Phi~(x) - log mu0(x))) (uniform
+ * u_6), solves the forward problem only for stage-2 candidates, and accepts
+ * with min(1, exp(Phi(x) - Phi(x_bar) + Phi~(x_bar) - Phi~(x))) (uniform
+ * u_7).  The surrogate must outlive its use by the chains. */
+rd_status rd_chains_set_surrogate(rd_chains* c, rd_surrogate* s);
 
 /* Blocks until all work enqueued on the problem's stream has finished. */
 rd_status rd_sync(rd_problem* p);

@@ -103,3 +103,76 @@ def surrogate_phi(params, theta, norm):
     x = features(np.atleast_2d(theta), norm["in_mu"], norm["in_sd"])
     out, _ = forward(params, x)
     return norm["floor"] + np.exp(norm["shift"] + norm["scale"] * out)
+
+
+# ---------------------------------------------------------------------------
+# Flat parameter layout of the GPU library (width W, 16 padded inputs):
+# W1 [W][16], b1 [W], W2 [W][W], b2 [W], W3 [W][W], b3 [W], W4 [W], b4 [1].
+# ---------------------------------------------------------------------------
+N_IN = 16
+
+
+def flat_layout(W):
+    sizes = [("W1", (W, N_IN)), ("b1", (W,)), ("W2", (W, W)), ("b2", (W,)),
+             ("W3", (W, W)), ("b3", (W,)), ("W4", (1, W)), ("b4", (1,))]
+    out, off = {}, 0
+    for name, shp in sizes:
+        n = int(np.prod(shp))
+        out[name] = (off, shp)
+        off += n
+    return out, off
+
+
+def unflatten(flat, W):
+    lay, _ = flat_layout(W)
+    get = lambda k: np.asarray(flat[lay[k][0]: lay[k][0] + int(np.prod(lay[k][1]))],
+                               dtype=np.float64).reshape(lay[k][1])
+    return [[get("W1"), get("b1")], [get("W2"), get("b2")], [get("W3"), get("b3")],
+            [get("W4"), get("b4")]]
+
+
+def flatten(params):
+    return np.concatenate([np.ravel(a) for layer in params for a in layer])
+
+
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even) via float32, as the GPU
+    rounds its FP32 values; returned as float64."""
+    b = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def loss_and_grads_bf16(params, x, target, rnd=bf16_round):
+    """MSE loss and gradients with the network evaluated at the precision the
+    tensor-core kernels use: BF16 inputs, weights W1-W3, hidden activations
+    and backpropagated dZ; FP32 (here FP64) accumulation, pre-activations
+    and the last layer.  With rnd = identity this is loss_and_grads."""
+    (W1, b1), (W2, b2), (W3, b3), (W4, b4) = params
+    B = x.shape[0]
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64) if rnd is not _ident else a
+    xb = rnd(x)
+    W1b, W2b, W3b = rnd(W1), rnd(W2), rnd(W3)
+    z1 = f32(xb @ W1b.T + b1)
+    h1 = rnd(silu(z1))
+    z2 = f32(h1 @ W2b.T + b2)
+    h2 = rnd(silu(z2))
+    z3 = f32(h2 @ W3b.T + b3)
+    h3 = rnd(silu(z3))
+    out = h3 @ W4[0] + b4[0]
+    err = out - target
+    loss = float(np.mean(err * err))
+    dout = 2.0 * err / B
+    dz3 = rnd(dout[:, None] * W4[0][None, :] * silu_grad(z3))
+    g = {"W4": (dout @ h3)[None, :], "b4": np.array([dout.sum()]),
+         "W3": dz3.T @ h2, "b3": dz3.sum(0)}
+    dz2 = rnd((dz3 @ W3b) * silu_grad(z2))
+    g["W2"], g["b2"] = dz2.T @ h1, dz2.sum(0)
+    dz1 = rnd((dz2 @ W2b) * silu_grad(z1))
+    g["W1"], g["b1"] = dz1.T @ xb, dz1.sum(0)
+    grads = [[g["W1"], g["b1"]], [g["W2"], g["b2"]], [g["W3"], g["b3"]], [g["W4"], g["b4"]]]
+    return loss, grads, out
+
+
+def _ident(a):
+    return np.asarray(a, dtype=np.float64)

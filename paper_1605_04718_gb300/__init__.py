@@ -28,6 +28,8 @@ RD_STEP_LINEAR, RD_STEP_LOG = 0, 1
 RD_PREC_F64, RD_PREC_F32 = 0, 1
 RD_MAX_SIZES, RD_MAX_OBS, RD_NPARAM = 4, 8, 5
 RD_NOALLOC_MAX_BATCH = 65536
+RD_SURROGATE_WIDTH = 256
+SURROGATE_IN = 16  # padded network inputs
 
 # Every entry point declared in include/rdbayes.h.
 EXPORTS = (
@@ -36,6 +38,9 @@ EXPORTS = (
     "rd_evaluate_batch_host", "rd_evaluate_batch_noalloc", "rd_chains_create", "rd_chains_destroy",
     "rd_chains_run", "rd_chains_read_samples", "rd_chains_get_state",
     "rd_chains_checkpoint", "rd_chains_restore", "rd_sync", "rd_last_error",
+    "rd_surrogate_create", "rd_surrogate_destroy", "rd_surrogate_train",
+    "rd_surrogate_predict", "rd_surrogate_loss_grad", "rd_surrogate_get_params",
+    "rd_surrogate_set_params", "rd_chains_set_surrogate",
 )
 
 
@@ -57,6 +62,15 @@ class rd_problem_desc(ctypes.Structure):
         ("prior_p0", ctypes.c_double * RD_NPARAM),
         ("prior_p1", ctypes.c_double * RD_NPARAM),
         ("step_space", ctypes.c_int * RD_NPARAM), ("w_max", ctypes.c_double),
+    ]
+
+
+class rd_train_desc(ctypes.Structure):
+    _fields_ = [
+        ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+        ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+        ("weight_decay", ctypes.c_double), ("holdout_frac", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
     ]
 
 
@@ -91,6 +105,15 @@ def load():
     L.rd_chains_checkpoint.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.rd_chains_restore.argtypes = [vp, vp, ctypes.c_size_t]
     L.rd_sync.argtypes = [vp]
+    L.rd_surrogate_create.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.rd_surrogate_destroy.argtypes = [vp]
+    L.rd_surrogate_train.argtypes = [vp, i, vp, vp, ctypes.POINTER(rd_train_desc), vp]
+    L.rd_surrogate_predict.argtypes = [vp, i, vp, vp]
+    L.rd_surrogate_loss_grad.argtypes = [vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.rd_surrogate_get_params.argtypes = [vp, vp, ctypes.c_size_t,
+                                          ctypes.POINTER(ctypes.c_size_t), vp]
+    L.rd_surrogate_set_params.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.rd_chains_set_surrogate.argtypes = [vp, vp]
     L.rd_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "rd_last_error":
@@ -268,3 +291,60 @@ def rd_sync(p):
 
 def rd_last_error():
     return load().rd_last_error().decode(errors="replace")
+
+
+# ----------------------------------------------------------------- surrogate
+def rd_surrogate_create(p, seed=0):
+    h = ctypes.c_void_p()
+    _check(load().rd_surrogate_create(p, ctypes.c_uint64(seed), ctypes.byref(h)))
+    return h
+
+
+def rd_surrogate_destroy(s):
+    _check(load().rd_surrogate_destroy(s))
+
+
+def rd_surrogate_train(s, theta, phi, epochs=30, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999,
+                       weight_decay=0.0, holdout_frac=0.1, seed=0):
+    """theta [n][P] float64, phi [n] float64: CUDA tensors.  Returns the report
+    (train MSE, hold-out MSE, hold-out mean relative Phi error, seconds)."""
+    td = rd_train_desc(epochs, batch, lr, beta1, beta2, weight_decay, holdout_frac, seed)
+    rep = np.zeros(4)
+    _check(load().rd_surrogate_train(s, theta.shape[0], _dev_ptr(theta), _dev_ptr(phi),
+                                     ctypes.byref(td), rep.ctypes.data_as(ctypes.c_void_p)))
+    return rep
+
+
+def rd_surrogate_predict(s, theta, phi_tilde):
+    _check(load().rd_surrogate_predict(s, theta.shape[0], _dev_ptr(theta), _dev_ptr(phi_tilde)))
+
+
+def rd_surrogate_loss_grad(s, theta, target, grads=None):
+    """target: float32 CUDA tensor [B]; grads: float32 CUDA tensor or None."""
+    loss = ctypes.c_double(0.0)
+    _check(load().rd_surrogate_loss_grad(s, theta.shape[0], _dev_ptr(theta), _dev_ptr(target),
+                                         ctypes.byref(loss), _dev_ptr(grads)))
+    return loss.value
+
+
+def rd_surrogate_get_params(s):
+    n = ctypes.c_size_t(0)
+    _check(load().rd_surrogate_get_params(s, None, 0, ctypes.byref(n), None))
+    buf = np.zeros(n.value, dtype=np.float32)
+    norm = np.zeros(2 * RD_NPARAM + 3)
+    _check(load().rd_surrogate_get_params(s, buf.ctypes.data_as(ctypes.c_void_p), n.value,
+                                          ctypes.byref(n), norm.ctypes.data_as(ctypes.c_void_p)))
+    return buf, norm
+
+
+def rd_surrogate_set_params(s, params=None, norm=None):
+    pp, pn = None, None
+    if params is not None:
+        params, pp = _host_ptr(params, np.float32)
+    if norm is not None:
+        norm, pn = _host_ptr(norm, np.float64)
+    _check(load().rd_surrogate_set_params(s, pp, 0 if params is None else params.size, pn))
+
+
+def rd_chains_set_surrogate(c, s):
+    _check(load().rd_chains_set_surrogate(c, s))

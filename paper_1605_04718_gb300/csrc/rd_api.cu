@@ -531,6 +531,19 @@ rd_status rd_chains_run(rd_chains* c, int n_steps) {
   return RD_OK;
 }
 
+rd_status rd_chains_set_surrogate(rd_chains* c, rd_surrogate* s) {
+  RD_CHECK(c, RD_EINVAL, "chains is NULL");
+  RD_CUDA(cudaStreamSynchronize(c->pb->stream));
+  c->sur = s;
+  c->graph_ready = false;  // the step graph differs with and without stage 1
+  if (s) {
+    RD_CUDA(mlp::ensure_rows(s, c->C));
+    RD_CUDA(mlp::predict(s, c->C, c->theta, c->phit, c->pb->stream));
+    RD_CUDA(cudaStreamSynchronize(c->pb->stream));
+  }
+  return RD_OK;
+}
+
 rd_status rd_chains_read_samples(rd_chains* c, double* out, size_t cap_steps,
                                  size_t* n_written, double* counters) {
   RD_CHECK(c, RD_EINVAL, "chains is NULL");

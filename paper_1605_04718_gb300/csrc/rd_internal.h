@@ -77,6 +77,7 @@ struct rd_chains {
   cudaGraphExec_t graph = nullptr;
   bool graph_ready = false;
   int graph_generation = -1;
+  rd_surrogate* sur = nullptr;  // delayed acceptance when set
 };
 
 namespace rd {
@@ -100,6 +101,11 @@ size_t simt2d_smem_bytes(int n);
 WorkQueue make_queue(const rd_problem* p);
 cudaError_t launch_solve(rd_problem* p, const double* theta, double* phi,
                          uint32_t* status, void* fields);
+
+namespace mlp {
+cudaError_t predict(rd_surrogate* s, int B, const double* theta, double* phit, cudaStream_t st);
+cudaError_t ensure_rows(rd_surrogate* s, int rows);
+}  // namespace mlp
 
 // chains
 cudaError_t launch_chain_init(rd_chains* c);

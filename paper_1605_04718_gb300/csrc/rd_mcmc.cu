@@ -7,7 +7,13 @@
 // ratio is the paper's rule for a non-flat prior (eq. (bayes)); parameters
 // stepped in log space carry the Jacobian theta in their density.
 // Random numbers: Philox4x32-10 at counters (chain, step, 0|1, 0), key = seed;
-// u_0..u_5 -> Box-Muller normals, u_6 -> acceptance uniform.
+// u_0..u_5 -> Box-Muller normals, u_6 -> acceptance uniform (stage-1 uniform
+// under delayed acceptance), u_7 -> stage-2 uniform.
+//
+// Delayed acceptance (Christen & Fox 2005, not in the paper): a surrogate
+// Phi~ screens each proposal; only stage-1 survivors are solved, and the
+// second test min(1, exp(Phi(x) - Phi(x_bar) + Phi~(x_bar) - Phi~(x))) keeps
+// the chain's stationary distribution the exact posterior.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -112,7 +118,11 @@ __global__ void k_chain_init(DevProblem pb, WorkQueue q, ChainView v) {
   }
 }
 
-__global__ void k_chain_propose(DevProblem pb, WorkQueue q, ChainView v) {
+// Stage-1 rejection marker (internal; never returned to callers).
+constexpr uint32_t kStage1Reject = 0x100u;
+
+// push = 0 (delayed acceptance): candidates are queued after stage 1.
+__global__ void k_chain_propose(DevProblem pb, WorkQueue q, ChainView v, int push) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= v.C) return;
   const uint32_t step = (uint32_t)v.ctl[0];
@@ -134,11 +144,58 @@ __global__ void k_chain_propose(DevProblem pb, WorkQueue q, ChainView v) {
   v.prop_lp[c] = lp;
   if (isfinite(lp)) {
     v.prop_status[c] = 0u;
-    queue_push(q, v.size_idx[c], c);
+    if (push) queue_push(q, v.size_idx[c], c);
   } else {
     v.prop_status[c] = RD_P_OUT_OF_SUPPORT;
     v.prop_phi[c] = (double)INFINITY;
   }
+}
+
+// Stage 1 of delayed acceptance: accept to stage 2 with probability
+// min(1, exp(-Phi~(x_bar) + lp(x_bar) + Phi~(x) - lp(x))); survivors are queued
+// for the exact solve.
+__global__ void k_chain_stage1(WorkQueue q, ChainView v) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.C) return;
+  if (v.prop_status[c] != 0u) return;  // outside the prior's support
+  double u[8];
+  chain_uniforms(v.seed, (uint32_t)c, (uint32_t)v.ctl[0], u);
+  const double la1 = (-v.prop_phit[c] + v.prop_lp[c]) - (-v.phit[c] + v.lp[c]);
+  if (log(u[6]) < la1) {
+    queue_push(q, v.size_idx[c], c);
+  } else {
+    v.prop_status[c] = kStage1Reject;
+    v.prop_phi[c] = (double)INFINITY;
+  }
+}
+
+// Stage 2: exact test on the survivors, then record the state.
+__global__ void k_chain_accept_da(ChainView v) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.C) return;
+  const int slot = v.ctl[1];
+  double u[8];
+  chain_uniforms(v.seed, (uint32_t)c, (uint32_t)v.ctl[0], u);
+  const uint32_t st = v.prop_status[c];
+  const bool pass1 = (st != RD_P_OUT_OF_SUPPORT && st != kStage1Reject);
+  bool acc = false;
+  if (st == 0u) {
+    const double la2 = (v.phi[c] - v.prop_phi[c]) + (v.prop_phit[c] - v.phit[c]);
+    acc = log(u[7]) < la2;
+  }
+  if (acc) {
+    for (int j = 0; j < v.P; ++j)
+      v.theta[(size_t)c * v.P + j] = v.prop[(size_t)c * v.P + j];
+    v.phi[c] = v.prop_phi[c];
+    v.lp[c] = v.prop_lp[c];
+    v.phit[c] = v.prop_phit[c];
+  }
+  for (int j = 0; j < v.P; ++j)
+    v.samples[((size_t)slot * v.P + j) * v.C + c] = v.theta[(size_t)c * v.P + j];
+  v.counters[c] += 1ull;
+  v.counters[(size_t)v.C + c] += pass1 ? 1ull : 0ull;
+  v.counters[(size_t)2 * v.C + c] += acc ? 1ull : 0ull;
+  v.counters[(size_t)3 * v.C + c] += pass1 ? 1ull : 0ull;
 }
 
 __global__ void k_chain_accept(DevProblem pb, ChainView v) {
@@ -200,12 +257,22 @@ cudaError_t launch_chain_step(rd_chains* c) {
   // the work lists may hold counts from an rd_evaluate_batch call in between
   cudaError_t e = cudaMemsetAsync(q.counts, 0, 2 * kMaxSizes * sizeof(int), p->stream);
   if (e != cudaSuccess) return e;
-  k_chain_propose<<<blocks, 128, 0, p->stream>>>(p->dev, q, v);
+  const int da = c->sur != nullptr;
+  k_chain_propose<<<blocks, 128, 0, p->stream>>>(p->dev, q, v, da ? 0 : 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (da) {
+    e = mlp::predict(c->sur, c->C, c->prop, c->prop_phit, p->stream);
+    if (e != cudaSuccess) return e;
+    k_chain_stage1<<<blocks, 128, 0, p->stream>>>(q, v);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   e = launch_solve(p, c->prop, c->prop_phi, c->prop_status, nullptr);
   if (e != cudaSuccess) return e;
-  k_chain_accept<<<blocks, 128, 0, p->stream>>>(p->dev, v);
+  if (da)
+    k_chain_accept_da<<<blocks, 128, 0, p->stream>>>(v);
+  else
+    k_chain_accept<<<blocks, 128, 0, p->stream>>>(p->dev, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_chain_advance<<<1, 32, 0, p->stream>>>(q, c->ctl);
   return cudaGetLastError();

@@ -101,3 +101,38 @@ def test_training_reduces_loss():
         opt.step(params, g)
     l1, _ = mlp.loss_and_grads(params, x, z)
     assert l1 < 0.2 * l0
+
+
+def test_bf16_round_matches_torch():
+    x = np.random.default_rng(9).standard_normal(10000) * 10.0 ** np.random.default_rng(10).uniform(-5, 5, 10000)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16_round(x), ref)
+
+
+def test_bf16_emulation_reduces_to_fp64_network():
+    """With the identity in place of BF16 rounding the emulated network is the
+    FP64 network (pinned against torch above); with rounding it stays close."""
+    rng = np.random.default_rng(11)
+    W = 32
+    params = mlp.init_params((mlp.N_IN, W, W, W, 1), 3)
+    for layer in params:
+        layer[1] += rng.normal(0, 0.1, layer[1].shape)
+    x = np.zeros((64, mlp.N_IN))
+    x[:, :4] = rng.standard_normal((64, 4))
+    z = rng.standard_normal(64)
+    l0, g0 = mlp.loss_and_grads(params, x, z)
+    l1, g1, _ = mlp.loss_and_grads_bf16(params, x, z, rnd=mlp._ident)
+    assert l1 == pytest.approx(l0, rel=1e-13)
+    for (a, b), (c, d) in zip(g0, g1):
+        assert np.allclose(a, c, rtol=1e-12, atol=1e-14) and np.allclose(b, d, rtol=1e-12, atol=1e-14)
+    l2, g2, _ = mlp.loss_and_grads_bf16(params, x, z)
+    assert l2 == pytest.approx(l0, rel=0.05)
+    flat0, flat2 = mlp.flatten(g0), mlp.flatten(g2)
+    assert np.linalg.norm(flat2 - flat0) < 0.05 * np.linalg.norm(flat0)
+
+
+def test_flat_layout_roundtrip():
+    W = 8
+    _, n = mlp.flat_layout(W)
+    flat = np.arange(n, dtype=np.float64)
+    assert np.array_equal(mlp.flatten(mlp.unflatten(flat, W)), flat)
