@@ -160,6 +160,114 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def ess_comparison(rd, torch, p, stream, dev, C_full, plain_step_s, steps=200, seed=0):
+    """ESS per second of plain and delayed-acceptance sampling on the bench
+    workload.  ESS per chain-step comes from 152-chain runs (one chain per SM)
+    started from a tuned pilot; the cost of a chain-step comes from timed
+    steps of C_full chains.  Returns a dict for the JSON line."""
+    from paper_1605_04718_gb300 import stats
+    t_total0 = time.perf_counter()
+    Cp = 152
+    # pilot: start near the mode, adapt the log-space steps towards an
+    # acceptance rate of 0.2-0.35 (per-parameter scales from the within-chain
+    # spread once chains move)
+    theta = np.asarray(rd_synth.chain_starts(TRUE4, Cp, seed=7000 + seed, rel=2e-4))
+    step = np.array([1e-4, 1e-4, 1e-4, 1e-4])
+    L = np.diag(step)
+    scale = 1.0
+    pilot = []
+    for rnd in range(10):
+        c = rd.rd_chains_create(p, theta, 9000 + rnd, step, capacity=25)
+        rd.rd_chains_set_proposal(c, scale * L)
+        rd.rd_chains_run(c, 25)
+        smp, cnt = rd.rd_chains_read_samples(c, 25, 4, Cp)
+        theta, _ = rd.rd_chains_get_state(c, 4, Cp)
+        rd.rd_chains_destroy(c)
+        acc = cnt[2] / max(cnt[0], 1)
+        pilot.append((acc, np.log(smp)))
+        scale *= 0.4 if acc < 0.05 else 0.7 if acc < 0.15 else 1.4 if acc > 0.4 else 1.0
+        if rnd >= 3:  # covariance of log theta from the last rounds, within-chain centred
+            lsm = np.concatenate([x[1] for x in pilot[-4:]], 0)
+            dev_ = (lsm - lsm.mean(0, keepdims=True)).transpose(1, 0, 2).reshape(4, -1)
+            cov = np.cov(dev_) + 1e-18 * np.eye(4)
+            L = np.linalg.cholesky(2.38 ** 2 / 4 * cov)
+            if rnd == 3:
+                scale = 1.0
+    lt = np.concatenate([x[1] for x in pilot[-4:]], 0).transpose(1, 0, 2).reshape(4, -1)
+    mu = lt.mean(1)
+    cov = np.cov(lt) + 1e-18 * np.eye(4)
+    Lc = np.linalg.cholesky(cov)
+    sdv = np.sqrt(np.diag(cov))
+    prop = scale * L
+    # training pairs from the batched exact solver around the pilot posterior
+    t0 = time.perf_counter()
+    n_train = 8192
+    rng = np.random.default_rng(11 + seed)
+    th_tr = np.exp(mu[None, :] + 2.5 * rng.standard_normal((n_train, 4)) @ Lc.T)
+    th_d = torch.tensor(th_tr, dtype=torch.float64, device=dev)
+    phi_d = torch.zeros(n_train, dtype=torch.float64, device=dev)
+    st_d = torch.zeros(n_train, dtype=torch.int32, device=dev)
+    rd.rd_evaluate_batch(p, th_d, phi_d, st_d)
+    rd.rd_sync(p)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sur = rd.rd_surrogate_create(p, seed=5)
+    rep = rd.rd_surrogate_train(sur, th_d, phi_d, epochs=60, batch=1024, lr=1e-3,
+                                holdout_frac=0.1, seed=3)
+    t_train = time.perf_counter() - t0
+    out = {"proposal_chol_log": prop.tolist(), "pilot_accept": [x[0] for x in pilot],
+           "posterior_sd_log": sdv.tolist(), "train_pairs": n_train,
+           "surrogate_holdout_rel_err": float(rep[2]), "t_datagen_s": t_gen,
+           "t_train_s": t_train}
+    # ESS per chain-step, plain and delayed acceptance, same starts
+    res = {}
+    for mode in ("plain", "da"):
+        c = rd.rd_chains_create(p, theta, 424242, step, capacity=steps)
+        rd.rd_chains_set_proposal(c, prop)
+        if mode == "da":
+            rd.rd_chains_set_surrogate(c, sur)
+        rd.rd_chains_run(c, steps)
+        smp, cnt = rd.rd_chains_read_samples(c, steps, 4, Cp)
+        rd.rd_chains_destroy(c)
+        summ = stats.summarize(smp, burn_frac=0.0, names=["a", "b", "d", "gamma"])
+        ess_min = min(x["ess"] for x in summ)
+        res[mode] = {"ess_per_chain_step": ess_min / (steps * Cp),
+                     "accept": cnt[2] / cnt[0], "solves_per_step": cnt[3] / cnt[0],
+                     "mean": [x["mean"] for x in summ], "rhat_max": max(x["rhat"] for x in summ)}
+    # cost of a full-batch delayed-acceptance step (4096 chains)
+    th_full = np.exp(mu[None, :] + np.random.default_rng(5).standard_normal((C_full, 4)) @ Lc.T)
+    c = rd.rd_chains_create(p, th_full, 777, step, capacity=4)
+    rd.rd_chains_set_proposal(c, prop)
+    rd.rd_chains_set_surrogate(c, sur)
+    rd.rd_chains_run(c, 1)
+    rd.rd_sync(p)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rd.rd_chains_run(c, 3)
+    e1.record(stream)
+    e1.synchronize()
+    da_step_s = e0.elapsed_time(e1) / 1e3 / 3
+    rd.rd_chains_destroy(c)
+    rd.rd_surrogate_destroy(sur)
+    plain_ess_s = res["plain"]["ess_per_chain_step"] * C_full / plain_step_s
+    da_ess_s = res["da"]["ess_per_chain_step"] * C_full / da_step_s
+    # amortised over a 5000-step run of C_full chains
+    run_steps = 5000
+    da_total = t_gen + t_train + run_steps * da_step_s
+    out.update({
+        "plain": res["plain"], "da": res["da"],
+        "plain_step_s_at_full_batch": plain_step_s, "da_step_s_at_full_batch": da_step_s,
+        "ess_per_s_plain": plain_ess_s, "ess_per_s_da": da_ess_s,
+        "ess_per_s_da_amortised_5000_steps": res["da"]["ess_per_chain_step"] * C_full * run_steps / da_total,
+        "da_vs_plain": da_ess_s / plain_ess_s,
+        "method": "ESS = min over (a,b,d,gamma) of the multi-chain ESS of 152 chains x "
+                  f"{steps} steps started from a pilot with an adapted proposal covariance "
+                  f"(Haario et al. 2001); cost per step from {C_full}-chain steps",
+        "t_wall_s": time.perf_counter() - t_total0,
+    })
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -285,7 +393,7 @@ def run_gpu(args):
                              "note": "16 N^2 B per proposal-step; state is resident in shared "
                                      "memory, so this is the HBM-normalised rate, not traffic"}
         line = {
-            "metric": "forward solves/s (128^2, 8000 IMEX steps/solve)",
+            "metric": "forward solves/s (128^2, 8000 IMEX steps/solve); ESS/s in 'ess_per_s'",
             "value": value, "unit": "forward solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -299,6 +407,11 @@ def run_gpu(args):
             "accept_rate": float(counters[2] / max(counters[0], 1)),
             "peaks_source": pk_src,
         }
+        if not args.no_ess:
+            line["ess"] = ess_comparison(rd, torch, p, stream, dev, C, t_all / args.steps)
+            line["ess_per_s"] = {"plain": line["ess"]["ess_per_s_plain"],
+                                 "da_surrogate": line["ess"]["ess_per_s_da"],
+                                 "da_surrogate_amortised": line["ess"]["ess_per_s_da_amortised_5000_steps"]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
@@ -320,6 +433,7 @@ def main():
     ap.add_argument("--e2e-reps", type=int, default=1)
     ap.add_argument("--ref-sample-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ess", action="store_true", help="skip the ESS/s comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -179,6 +179,13 @@ rd_status rd_chains_create(rd_problem* p, int n_chains, const double* theta0,
                            rd_chains** out);
 rd_status rd_chains_destroy(rd_chains* c);
 
+/* Replaces the random-walk increments by a correlated Gaussian: the proposal
+ * in step space is eta + L xi with L (host, [n_params][n_params], row-major,
+ * lower-triangular; entries above the diagonal are ignored) and xi the chain's
+ * standard normals.  The walk stays symmetric, so Algorithm 1's acceptance is
+ * unchanged.  L = diag(step) is the sampler rd_chains_create sets up. */
+rd_status rd_chains_set_proposal(rd_chains* c, const double* L);
+
 /* Advances every chain by n_steps (async; graph-replayed per step).
  * ESTATE if the sample buffer would overflow. */
 rd_status rd_chains_run(rd_chains* c, int n_steps);

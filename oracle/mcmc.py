@@ -40,6 +40,7 @@ class Model:
     prior_p1: np.ndarray       # uniform: upper bound; lognormal: sigma of log
     step_space: list           # per inferred parameter: "linear" | "log"
     step: np.ndarray           # random-walk standard deviation in step space
+    chol: np.ndarray = None    # optional lower-triangular L: eta_bar = eta + L xi
     extra: dict = field(default_factory=dict)
 
     @property
@@ -138,7 +139,10 @@ class Chains:
         """One step of Algorithm 1 (or its delayed-acceptance form)."""
         m = self.model
         xi, uu = chain_randoms(self.seed, self.C, self.step_index)
-        eta_bar = m.to_eta(self.theta) + xi[:, : m.P] * np.asarray(m.step)[None, :]
+        if m.chol is not None:  # correlated Gaussian random walk, increment L xi
+            eta_bar = m.to_eta(self.theta) + xi[:, : m.P] @ np.asarray(m.chol).T
+        else:
+            eta_bar = m.to_eta(self.theta) + xi[:, : m.P] * np.asarray(m.step)[None, :]
         th_bar = m.to_theta(eta_bar)
         lp_bar = m.log_prior_eta(th_bar)
         in_support = np.isfinite(lp_bar)

@@ -40,7 +40,7 @@ EXPORTS = (
     "rd_chains_checkpoint", "rd_chains_restore", "rd_sync", "rd_last_error",
     "rd_surrogate_create", "rd_surrogate_destroy", "rd_surrogate_train",
     "rd_surrogate_predict", "rd_surrogate_loss_grad", "rd_surrogate_get_params",
-    "rd_surrogate_set_params", "rd_chains_set_surrogate",
+    "rd_surrogate_set_params", "rd_chains_set_surrogate", "rd_chains_set_proposal",
 )
 
 
@@ -114,6 +114,7 @@ def load():
                                           ctypes.POINTER(ctypes.c_size_t), vp]
     L.rd_surrogate_set_params.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.rd_chains_set_surrogate.argtypes = [vp, vp]
+    L.rd_chains_set_proposal.argtypes = [vp, vp]
     L.rd_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "rd_last_error":
@@ -348,3 +349,9 @@ def rd_surrogate_set_params(s, params=None, norm=None):
 
 def rd_chains_set_surrogate(c, s):
     _check(load().rd_chains_set_surrogate(c, s))
+
+
+def rd_chains_set_proposal(c, L):
+    """L: [P][P] lower-triangular factor of the random-walk covariance (step space)."""
+    L, pl = _host_ptr(L, np.float64)
+    _check(load().rd_chains_set_proposal(c, pl))

@@ -446,7 +446,10 @@ rd_status rd_chains_create(rd_problem* p, int n_chains, const double* theta0,
   c->P = p->desc.n_params;
   c->seed = seed;
   c->capacity = capacity;
-  for (int j = 0; j < c->P; ++j) c->step[j] = step[j];
+  for (int j = 0; j < c->P; ++j) {
+    c->step[j] = step[j];
+    c->chol[j * RD_NPARAM + j] = step[j];
+  }
   const size_t C = (size_t)n_chains, P = (size_t)c->P;
   bool ok = cudaMalloc(&c->theta, sizeof(double) * C * P) == cudaSuccess &&
             cudaMalloc(&c->phi, sizeof(double) * C) == cudaSuccess &&
@@ -528,6 +531,18 @@ rd_status rd_chains_run(rd_chains* c, int n_steps) {
   }
   for (int s = 0; s < n_steps; ++s) RD_CUDA(cudaGraphLaunch(c->graph, c->pb->stream));
   c->ring_host += n_steps;
+  return RD_OK;
+}
+
+rd_status rd_chains_set_proposal(rd_chains* c, const double* L) {
+  RD_CHECK(c && L, RD_EINVAL, "NULL argument");
+  for (int j = 0; j < c->P; ++j)
+    for (int i = 0; i < RD_NPARAM; ++i) {
+      const double v = (i <= j && i < c->P) ? L[j * c->P + i] : 0.0;
+      RD_CHECK(isfinite(v), RD_EINVAL, "proposal factor must be finite");
+      c->chol[j * RD_NPARAM + i] = v;
+    }
+  c->graph_ready = false;  // captured kernels hold the factor by value
   return RD_OK;
 }
 

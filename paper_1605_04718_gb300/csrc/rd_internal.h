@@ -60,6 +60,7 @@ struct rd_chains {
   int capacity = 0;
   int ring_host = 0;  // samples in the device ring (host mirror)
   double step[RD_NPARAM] = {0, 0, 0, 0, 0};
+  double chol[RD_NPARAM * RD_NPARAM] = {};  // proposal increments L xi (row-major)
   // device state
   double* theta = nullptr;      // [C][P]
   double* phi = nullptr;        // [C]

@@ -25,7 +25,7 @@ namespace rd {
 struct ChainView {
   int C, P;
   uint64_t seed;
-  double step[kNParam];
+  double chol[kNParam * kNParam];  // lower-triangular proposal factor
   double* theta;
   double* phi;
   double* phit;
@@ -46,7 +46,7 @@ static ChainView view_of(const rd_chains* c) {
   v.C = c->C;
   v.P = c->P;
   v.seed = c->seed;
-  for (int j = 0; j < kNParam; ++j) v.step[j] = c->step[j];
+  for (int j = 0; j < kNParam * kNParam; ++j) v.chol[j] = c->chol[j];
   v.theta = c->theta;
   v.phi = c->phi;
   v.phit = c->phit;
@@ -132,11 +132,13 @@ __global__ void k_chain_propose(DevProblem pb, WorkQueue q, ChainView v, int pus
   double th[kNParam];
   for (int j = 0; j < v.P; ++j) {
     const double t = v.theta[(size_t)c * v.P + j];
+    double inc = 0.0;  // (L xi)_j
+    for (int i = 0; i <= j; ++i) inc += v.chol[j * kNParam + i] * xi[i];
     double tb;
     if (pb.step_space[j] == RD_STEP_LOG)
-      tb = exp(log(t) + v.step[j] * xi[j]);
+      tb = exp(log(t) + inc);
     else
-      tb = t + v.step[j] * xi[j];
+      tb = t + inc;
     th[j] = tb;
     v.prop[(size_t)c * v.P + j] = tb;
   }

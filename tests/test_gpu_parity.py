@@ -100,6 +100,28 @@ def test_1d_chains_match_oracle_trajectories():
     rd.rd_problem_destroy(p)
 
 
+def test_1d_chains_with_correlated_proposal_match_oracle():
+    """Proposal increments L xi with a full lower-triangular L: the same
+    samples on both sides (FP64, same Philox streams)."""
+    p, P = _problem_1d()
+    C, S = 4, 200
+    L = np.array([[0.01, 0.0], [0.006, 0.008]])
+    theta0 = rd_synth.chain_starts([0.1, 0.9], C, seed=101)
+    c = rd.rd_chains_create(p, theta0, 4321, [0.01, 0.01], capacity=S)
+    rd.rd_chains_set_proposal(c, L)
+    rd.rd_chains_run(c, S)
+    s_gpu, counters = rd.rd_chains_read_samples(c, S, 2, C)
+    m = mcmc.Model([0, 1], np.array([0.1, 0.9, 10.0, 200.0, 0.0]), ["uniform"] * 2,
+                   np.array([0.0, 0.0]), np.array([1.0, 2.0]), ["linear"] * 2,
+                   np.array([0.01, 0.01]), chol=L)
+    ch = mcmc.Chains(m, theta0, 4321, lambda th: P.forward_batch(th))
+    s_orc = ch.run(S)
+    assert np.allclose(s_gpu, s_orc, rtol=1e-9, atol=1e-12)
+    assert counters[2] == ch.n_acc
+    rd.rd_chains_destroy(c)
+    rd.rd_problem_destroy(p)
+
+
 # ------------------------------------------------------------------ 2-D FP32
 @pytest.mark.parametrize("n,n_steps", [(16, 400), (32, 400), (48, 300), (64, 200)])
 def test_2d_fields_and_phi_match_oracle(n, n_steps):

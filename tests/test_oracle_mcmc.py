@@ -177,3 +177,15 @@ def test_summarize_credible_interval():
     assert out["q025"][0] == pytest.approx(-1.96, abs=0.05)
     assert out["q975"][0] == pytest.approx(1.96, abs=0.05)
     assert abs(out["mean"][0]) < 0.03
+
+
+def test_correlated_proposal_keeps_posterior():
+    """A lower-triangular proposal factor L (increment L xi) is still a
+    symmetric random walk: the linear-Gaussian posterior is unchanged."""
+    mean, cov = _toy_posterior()
+    m = _toy_model()
+    m.chol = np.linalg.cholesky(2.38**2 / 2 * cov)
+    ch = mcmc.Chains(m, np.tile(mean, (32, 1)) + 0.1, seed=13, phi_fn=_toy_phi)
+    samples = ch.run(1500)
+    _check_gaussian(samples, mean, cov)
+    assert 0.2 < ch.n_acc / ch.n_prop < 0.6
