@@ -29,6 +29,8 @@ import rd_synth  # noqa: E402
 DATASET = "rd2d_n128"
 TRUE4 = [0.1, 0.9, 10.0, 200.0]
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# RD_KERNEL_* of include/rdbayes.h
+KERNELS = {"simt": 1, "stacked": 2, "resident": 3}
 
 
 def peaks():
@@ -298,6 +300,8 @@ def run_gpu(args):
                         [0.5] * 4, [rd.RD_STEP_LOG] * 4, solver=solver)
     stream = torch.cuda.current_stream(dev)
     p = rd.rd_problem_create(desc, stream)
+    if args.kernel != "default":
+        rd.rd_set_size_kernel(p, 0, KERNELS[args.kernel])
     rd.rd_set_initial_state(p, 0, ds["u0"].astype(np.float64), ds["v0"].astype(np.float64))
     rd.rd_set_observations(p, 0, ds["obs_steps"], spec["field_mask"],
                            ds["y"].astype(np.float64), spec["sigma"])
@@ -374,7 +378,8 @@ def run_gpu(args):
         flop_per_solve = 16.0 * n**3 * spec["n_steps"]  # 4 transforms x 2 N^3 x 2 fields / step
         bytes_per_solve = 16.0 * n * n * spec["n_steps"]  # u, v FP32 read + write per step
         clk = ck.get("sm_mhz") or 1900.0
-        if solver == rd.RD_SOLVER_DCT_SIMT:
+        kind = rd.rd_get_size_kernel(p, 0)
+        if kind == rd.RD_KERNEL_SIMT:
             achieved = flop_per_solve * C / k_dur / 1e12
             fp32_peak = 152 * 128 * 2 * (ck.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -385,7 +390,9 @@ def run_gpu(args):
             achieved = flop_per_solve * C / k_dur / 1e12
             tpk = _find(pk, "bf16_tflops") or FALLBACK_PEAKS["bf16_tflops"]
             roof = {"bound": "tensor", "achieved": achieved, "peak": tpk, "unit": "TFLOP/s",
-                    "frac": achieved / tpk, "traffic": None, "kernel": "k_solve2d_tc",
+                    "frac": achieved / tpk, "traffic": None,
+                    "kernel": ("k_solve2d_tc128<2>" if kind == rd.RD_KERNEL_TC_RESIDENT
+                               else "k_solve2d_tc<128>"),
                     "kernel_ms": 1e3 * k_dur, "peak_source": f"{pk_src} bf16 burst (= fp16 rate)"}
         hbm = _find(pk, "hbm_gbs", "hbm_GBps", "copy_gbs") or FALLBACK_PEAKS["hbm_gbs"]
         roof["hbm_equiv"] = {"gbs": bytes_per_solve * C / k_dur / 1e9, "peak_gbs": hbm,
@@ -429,6 +436,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--chains", type=int, default=4096)
     ap.add_argument("--solver", default="auto", choices=["auto", "simt", "tc"])
+    ap.add_argument("--kernel", default="default", choices=["default"] + sorted(KERNELS),
+                    help="solve kernel of the 128^2 size (default: the library's choice)")
     ap.add_argument("--kernel-reps", type=int, default=2)
     ap.add_argument("--e2e-reps", type=int, default=1)
     ap.add_argument("--ref-sample-steps", type=int, default=300)

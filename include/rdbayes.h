@@ -70,6 +70,20 @@ enum {
   RD_SOLVER_DCT_TC = 3     /* 2-D eigenbasis solve, split-FP16 tcgen05 GEMMs */
 };
 
+/* Solve kernel of one 2-D grid size (rd_set_size_kernel, rd_autotune).  All
+ * compute the same IMEX step; they differ in how the eigenbasis transforms of
+ * the implicit solve run on the GPU. */
+enum {
+  RD_KERNEL_DEFAULT = 0,     /* from desc.solver: SIMT for RD_SOLVER_DCT_SIMT;
+                                otherwise TC_RESIDENT at N = 128, else
+                                TC_STACKED */
+  RD_KERNEL_SIMT = 1,        /* FP32 CUDA-core GEMMs, one proposal per CTA */
+  RD_KERNEL_TC_STACKED = 2,  /* split-FP16 tcgen05, DCT matrix in shared memory,
+                                floor(128/N) proposals stacked per MMA tile */
+  RD_KERNEL_TC_RESIDENT = 3  /* split-FP16 tcgen05, DCT matrices resident in
+                                tensor memory; N = 128 only */
+};
+
 enum { RD_PRIOR_UNIFORM = 0, RD_PRIOR_LOGNORMAL = 1 };
 enum { RD_STEP_LINEAR = 0, RD_STEP_LOG = 1 };
 enum { RD_PREC_F64 = 0, RD_PREC_F32 = 1 };
@@ -164,6 +178,16 @@ rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
 rd_status rd_evaluate_batch_noalloc(rd_problem* p, int B, const double* theta,
                                     const int* size_idx, double* loglik,
                                     uint32_t* status, void* fields);
+
+/* Kernel that solves the proposals of grid size `size_idx` (RD_KERNEL_*).
+ * Sizes that share a kernel run in one persistent launch; a batch whose sizes
+ * use different kernels runs one launch per kernel, in stream order.  EINVAL
+ * for a 1-D problem (always the Thomas solve), an unknown kernel, or
+ * TC_RESIDENT at N != 128.  Takes effect at the next launch (captured chain
+ * steps are re-captured). */
+rd_status rd_set_size_kernel(rd_problem* p, int size_idx, int kernel);
+/* The kernel size `size_idx` runs with, RD_KERNEL_DEFAULT resolved. */
+rd_status rd_get_size_kernel(const rd_problem* p, int size_idx, int* kernel);
 
 /* Chains: n_chains independent random-walk Metropolis chains advanced in
  * lock-step, one proposal per chain per step (Algorithm 1).

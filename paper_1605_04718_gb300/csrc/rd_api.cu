@@ -49,20 +49,47 @@ WorkQueue make_queue(const rd_problem* p) {
 }
 
 bool uses_tc(const rd_problem* p) {
-  return p->desc.dim == 2 &&
-         (p->desc.solver == RD_SOLVER_DCT_TC || p->desc.solver == RD_SOLVER_AUTO);
+  if (p->desc.dim != 2) return false;
+  for (int s = 0; s < p->desc.n_sizes; ++s)
+    if (kernel_for_size(p, s) != RD_KERNEL_SIMT) return true;
+  return false;
+}
+
+int kernel_for_size(const rd_problem* p, int s) {
+  if (p->desc.dim != 2) return RD_KERNEL_SIMT;
+  const int k = p->kernel_of_size[s];
+  if (k != RD_KERNEL_DEFAULT) return k;
+  if (p->desc.solver == RD_SOLVER_DCT_SIMT) return RD_KERNEL_SIMT;
+  return p->desc.nx[s] == 128 ? RD_KERNEL_TC_RESIDENT : RD_KERNEL_TC_STACKED;
+}
+
+cudaError_t launch_solve_queue(rd_problem* p, const WorkQueue& q, const double* theta,
+                               double* phi, uint32_t* status, void* fields, cudaStream_t st) {
+  static const int kinds[3] = {RD_KERNEL_TC_RESIDENT, RD_KERNEL_TC_STACKED, RD_KERNEL_SIMT};
+  for (int kind : kinds) {
+    WorkQueue sub = q;  // the sizes of this kernel, largest grid first
+    sub.n_sizes = 0;
+    for (int k = 0; k < q.n_sizes; ++k)
+      if (kernel_for_size(p, q.order[k]) == kind) sub.order[sub.n_sizes++] = q.order[k];
+    if (sub.n_sizes == 0) continue;
+    cudaError_t e;
+    if (kind == RD_KERNEL_TC_RESIDENT)
+      e = launch_solve_tc128(p->dev, sub, theta, phi, status, fields, grid_solve_tc128(p->n_sm),
+                             p->ws.err, st);
+    else if (kind == RD_KERNEL_TC_STACKED)
+      e = launch_solve_tc(p->dev, sub, theta, phi, status, fields,
+                          grid_solve_tc(p->dev.max_n, p->n_sm), p->ws.err, st);
+    else
+      e = launch_solve_simt(p->dev, sub, theta, phi, status, fields,
+                            grid_solve_simt(p->desc.dim, p->dev.max_n, p->n_sm), st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_solve_on(rd_problem* p, const double* theta, double* phi,
                             uint32_t* status, void* fields, cudaStream_t st) {
-  if (uses_tc(p)) {
-    const int grid = grid_solve_tc(p->dev.max_n, p->n_sm);
-    return launch_solve_tc(p->dev, make_queue(p), theta, phi, status, fields, grid,
-                           p->ws.err, st);
-  }
-  const int grid = grid_solve_simt(p->desc.dim, p->dev.max_n, p->n_sm);
-  return launch_solve_simt(p->dev, make_queue(p), theta, phi, status, fields,
-                           grid, st);
+  return launch_solve_queue(p, make_queue(p), theta, phi, status, fields, st);
 }
 
 cudaError_t launch_solve(rd_problem* p, const double* theta, double* phi,
@@ -210,8 +237,11 @@ rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
     rd_problem_destroy(p);
     return RD_ENOMEM;
   }
+  bool has128 = false;
+  for (int k = 0; k < desc->n_sizes; ++k) has128 = has128 || (desc->dim == 2 && desc->nx[k] == 128);
   if (setup_solve_simt(desc->dim, dv.max_n) != cudaSuccess ||
-      (uses_tc(p) && setup_solve_tc(dv.max_n) != cudaSuccess)) {
+      (desc->dim == 2 && setup_solve_tc(dv.max_n) != cudaSuccess) ||
+      (has128 && setup_solve_tc128() != cudaSuccess)) {
     rd_problem_destroy(p);
     set_error("cannot configure the solve kernels' shared memory");
     return RD_ECUDA;
@@ -348,6 +378,28 @@ rd_status rd_evaluate_batch(rd_problem* p, int B, const double* theta,
   WorkQueue q = make_queue(p);
   RD_CUDA(launch_fill_queue(q, B, size_idx, loglik, status, p->stream));
   RD_CUDA(launch_solve(p, theta, loglik, status, fields));
+  return RD_OK;
+}
+
+rd_status rd_set_size_kernel(rd_problem* p, int size_idx, int kernel) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(p->desc.dim == 2, RD_EINVAL, "1-D problems always use the Thomas solve");
+  RD_CHECK(size_idx >= 0 && size_idx < p->desc.n_sizes, RD_EINVAL, "size_idx out of range");
+  RD_CHECK(kernel >= RD_KERNEL_DEFAULT && kernel <= RD_KERNEL_TC_RESIDENT, RD_EINVAL,
+           "unknown kernel");
+  RD_CHECK(kernel != RD_KERNEL_TC_RESIDENT || p->desc.nx[size_idx] == 128, RD_EINVAL,
+           "RD_KERNEL_TC_RESIDENT needs N = 128");
+  if (p->kernel_of_size[size_idx] != kernel) {
+    p->kernel_of_size[size_idx] = kernel;
+    ++p->generation;  // captured chain steps hold the old launches
+  }
+  return RD_OK;
+}
+
+rd_status rd_get_size_kernel(const rd_problem* p, int size_idx, int* kernel) {
+  RD_CHECK(p && kernel, RD_EINVAL, "NULL argument");
+  RD_CHECK(size_idx >= 0 && size_idx < p->desc.n_sizes, RD_EINVAL, "size_idx out of range");
+  *kernel = kernel_for_size(p, size_idx);
   return RD_OK;
 }
 

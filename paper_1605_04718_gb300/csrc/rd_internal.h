@@ -43,7 +43,8 @@ struct rd_problem {
   // bumped whenever a device buffer that a captured graph may reference is
   // replaced; chains re-capture their step graph when it changes
   int generation = 0;
-  int solver_per_size[RD_MAX_SIZES] = {0, 0, 0, 0};
+  // RD_KERNEL_* of each size; RD_KERNEL_DEFAULT follows desc.solver
+  int kernel_of_size[RD_MAX_SIZES] = {0, 0, 0, 0};
   // staging for rd_evaluate_batch_host
   double* h2d_theta = nullptr;
   int* h2d_size = nullptr;
@@ -95,11 +96,24 @@ cudaError_t launch_solve_tc(const DevProblem& pb, const WorkQueue& q, const doub
                             double* phi, uint32_t* status, void* fields, int grid, int* err,
                             cudaStream_t st);
 size_t tc_smem_bytes_host(int max_n);
+// 128^2-only tensor-core solve with the DCT matrices resident in TMEM
+// (rd_solve_tc2.cu): every size in its queue must be a 2-D 128^2 grid.
+bool tc128_applicable(const DevProblem& pb, int size_idx);
+cudaError_t setup_solve_tc128();
+int grid_solve_tc128(int n_sm);
+cudaError_t launch_solve_tc128(const DevProblem& pb, const WorkQueue& q, const double* theta,
+                               double* phi, uint32_t* status, void* fields, int grid, int* err,
+                               cudaStream_t st);
 bool uses_tc(const rd_problem* p);
 int grid_solve_simt(int dim, int max_n, int n_sm);
 size_t simt2d_smem_bytes(int n);
 
 WorkQueue make_queue(const rd_problem* p);
+int kernel_for_size(const rd_problem* p, int size_idx);
+// Launches the solve kernels over the queue's sizes, one persistent launch
+// per kernel kind in use (sizes grouped by kernel_for_size).
+cudaError_t launch_solve_queue(rd_problem* p, const WorkQueue& q, const double* theta,
+                               double* phi, uint32_t* status, void* fields, cudaStream_t st);
 cudaError_t launch_solve(rd_problem* p, const double* theta, double* phi,
                          uint32_t* status, void* fields);
 

@@ -99,12 +99,7 @@ extern "C" rd_status rd_evaluate_batch_noalloc(rd_problem* p, int B, const doubl
   // launch_fill_queue zeroes the counters left by the previous call first
   cudaError_t e = launch_fill_queue(q, B, size_idx, loglik, status, p->stream);
   if (e == cudaSuccess) {
-    if (uses_tc(p))
-      e = launch_solve_tc(p->dev, q, theta, loglik, status, fields,
-                          grid_solve_tc(p->dev.max_n, p->n_sm), p->ws.err, p->stream);
-    else
-      e = launch_solve_simt(p->dev, q, theta, loglik, status, fields,
-                            grid_solve_simt(p->desc.dim, p->dev.max_n, p->n_sm), p->stream);
+    e = launch_solve_queue(p, q, theta, loglik, status, fields, p->stream);
   }
   if (e != cudaSuccess) {
     set_error(std::string("rd_evaluate_batch_noalloc: launch failed: ") + cudaGetErrorString(e));

@@ -17,6 +17,7 @@
 
 #include "rd_common.cuh"
 #include "rd_internal.h"
+#include "rd_tc_ptx.cuh"
 
 namespace rd {
 
@@ -211,7 +212,7 @@ __device__ __forceinline__ void implicit_solve_simt(float* W, const float* Cm,
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TM; ++j) acc[i][j] = acc[i][j] / fmaf(beta, mur[i] + muc[j], alpha);
+    for (int j = 0; j < TM; ++j) acc[i][j] *= tc::recip_nr(fmaf(beta, mur[i] + muc[j], alpha));
   __syncthreads();
   store_tile<N>(W, acc, ty, tx);
   __syncthreads();

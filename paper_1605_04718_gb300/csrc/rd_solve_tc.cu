@@ -104,7 +104,17 @@ __device__ __forceinline__ void store_zero8(uint8_t* hi_tile, uint8_t* lo_tile, 
   *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(0, 0, 0, 0);
 }
 
-// Issues one stage (3 split products over K = n in steps of 16) of field f.
+// Compensation of the tensor core's round-toward-zero accumulation: each
+// MMA's sum is truncated toward zero, about 0.72 * 2^-24 of the accumulator
+// per MMA; with the correction products issued first (small accumulator) the
+// n / 16 main products of a stage leave a shrink of about (n / 16) * 0.5 *
+// 2^-24 (partial sums average about 0.7 of the final value), undone by
+// scaling each stage's output by 1 + kappa.
+__device__ __forceinline__ float tc_rz_comp(int n) { return (float)n * 0x1p-29f; }
+
+// Issues one stage of field f (3 split products over K = n in steps of 16):
+// the correction products (hi*lo, lo*hi) of every K block first, while the
+// accumulator is small, then the main products (hi*hi).
 __device__ __forceinline__ void issue_stage(uint8_t* base, int nmax, int n, int stage, int f,
                                             uint32_t d_tmem) {
   const int a_mn = (stage == 2 || stage == 4) ? 1 : 0;
@@ -123,9 +133,14 @@ __device__ __forceinline__ void issue_stage(uint8_t* base, int nmax, int n, int 
     const uint64_t al = sdesc_sw128(a_lo + a_off, a_lbo, 1024u);
     const uint64_t bh = sdesc_sw128(b_hi + b_off, b_lbo, 1024u);
     const uint64_t bl = sdesc_sw128(b_lo + b_off, b_lbo, 1024u);
-    mma_f16(d_tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
-    mma_f16(d_tmem, ah, bl, idesc, 1u);
+    mma_f16(d_tmem, ah, bl, idesc, kk > 0 ? 1u : 0u);
     mma_f16(d_tmem, al, bh, idesc, 1u);
+  }
+  for (int kk = 0; kk < n / 16; ++kk) {  // main products last (see tc_rz_comp)
+    const uint32_t a_off = a_mn ? (uint32_t)kk * 2048u : (uint32_t)(kk >> 2) * 16384u + (kk & 3) * 32u;
+    const uint32_t b_off = b_mn ? (uint32_t)kk * 2048u : (uint32_t)(kk >> 2) * cstride + (kk & 3) * 32u;
+    mma_f16(d_tmem, sdesc_sw128(a_hi + a_off, a_lbo, 1024u), sdesc_sw128(b_hi + b_off, b_lbo, 1024u),
+            idesc, 1u);
   }
 }
 
@@ -179,6 +194,7 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
   double phi = 0.0;
   int bad = 0;
   int next_obs = 0;
+  const float kap = tc_rz_comp(n);
   for (int step = 0;; ++step) {
     if (step > 0) {
       if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
@@ -191,6 +207,7 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     }
     const bool last = (step == pb.n_steps);
     const bool obs = next_obs < S.n_obs && step == S.obs_steps[next_obs];
+    const float kap_w = step > 0 ? kap : 0.f;  // the initial state is exact
     // growth factors of this step (FP64, rounded once)
     float alpha = 1.f, cu = 0.f, cv = 0.f, beta_f = 0.f;
     if (pb.growth) {
@@ -210,8 +227,8 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
       float du[8], dv[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        du[j] = wu[j] * (1.f / 128.f);
-        dv[j] = wv[j] * (1.f / 128.f);
+        du[j] = fmaf(wu[j] * (1.f / 128.f), kap_w, wu[j] * (1.f / 128.f));
+        dv[j] = fmaf(wv[j] * (1.f / 128.f), kap_w, wv[j] * (1.f / 128.f));
       }
       if (valid && (obs || last)) {
         if (obs) {
@@ -272,7 +289,7 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
       tmem_wait_ld();
       if (!lane_used) continue;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a8[j] *= (1.f / 128.f);
+      for (int j = 0; j < 8; ++j) a8[j] = fmaf(a8[j] * (1.f / 128.f), kap, a8[j] * (1.f / 128.f));
       store_split8(op_hi[f], op_lo[f], n, row, p * n + k, a8);
     }
     fence_proxy_async_smem();
@@ -295,8 +312,10 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
       }
       if (pb.growth) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          l8[j] = (1.f / 64.f) / fmaf(beta_f, ctl->mu[c + j] + mu_row, alpha);
+        for (int j = 0; j < 8; ++j) {
+          l8[j] = (1.f / 64.f) * recip_nr(fmaf(beta_f, ctl->mu[c + j] + mu_row, alpha));
+          l8[j] = fmaf(l8[j], kap, l8[j]);
+        }
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) a8[j] *= l8[j];
@@ -316,6 +335,8 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
       tmem_ld8(t_acc_f + (uint32_t)y, a8);
       tmem_wait_ld();
       if (!lane_used) continue;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a8[j] = fmaf(a8[j], kap, a8[j]);
       store_split8(op_hi[f], op_lo[f], n, row, p * n + y, a8);
     }
     fence_proxy_async_smem();
@@ -367,8 +388,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_solve2d_tc(DevProblem pb, WorkQueue q, const double* theta, double* phi, uint32_t* status,
                  float* fields, size_t field_stride, int* err) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  // 1024-byte aligned start, derived from smem_raw so that the compiler keeps
+  // the shared address space (plain shared loads and stores, not generic)
+  uint8_t* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   TcCtrl* ctl = reinterpret_cast<TcCtrl*>(base + tc_off_ctrl(NMAX));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr uint32_t kCols = tc_tmem_cols(NMAX);
@@ -452,6 +474,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int j = 0; j < 8; ++j) {
           v8[j] = lane_used ? (w0[(size_t)row * n + x + j] - ref) * 128.f : 0.f;
           l8[j] = (1.f / 64.f) / fmaf(beta, ctl->mu[x + j] + mu_row, 1.f);
+          l8[j] = fmaf(l8[j], tc_rz_comp(n), l8[j]);
         }
         __syncwarp();
         tmem_st8(tmem + lane_off + (uint32_t)(f * n + x), v8);

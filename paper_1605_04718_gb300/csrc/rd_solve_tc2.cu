@@ -1,0 +1,568 @@
+// rd_solve_tc2.cu -- the 128^2 forward solve on the tensor cores with the
+// DCT matrices resident in TMEM.
+//
+// Same step and number format as k_solve2d_tc (rd_solve_tc.cu): explicit
+// reaction, implicit diffusion by the four eigenbasis transforms (Sec. 3.1.1
+// with the diagonal solve in the DCT-II basis), split-FP16 operands with
+// three products, FP32 accumulation, state held as deviation from the
+// initial-state mean.  The difference is the orientation: the constant
+// matrix 8C (and its transpose) is operand A, read from TMEM, and each
+// field's data is operand B in shared memory, so an MMA reads 4 KB of
+// operands from shared memory instead of 8 KB.  With i the index on TMEM
+// lanes and j the one on columns:
+//   stage 1  D[k][i] = sum_j C[k][j] R[i][j]        (B = R, K-major)
+//   stage 2  D[l][k] = sum_i C[l][i] P[k][i]        (B = P, K-major)
+//   scale    S[l][k] = D[l][k] L[l][k]
+//   stage 3  D[i][k] = sum_l C^T[i][l] S[l][k]      (B = S, MN-major)
+//   stage 4  D[j][i] = sum_k C^T[j][k] E[i][k]      (B = E, K-major)
+// so one step maps a state with i on the lanes to one with j on the lanes:
+// the state is W (y on the lanes) after an even number of steps and W^T
+// after an odd number.  L is symmetric, so the same code serves both.
+//
+// Pipelining.  The fields u and v run interleaved: while the tensor core
+// works on one field's stage, the other field's converter warps turn the
+// previous result into the next operand.  Stage 3 is also split into two
+// N halves, so its first half starts while the second half of its operand
+// is still being written.
+//
+// The diagonal factor L (times 1/64 and the compensation below) of a fixed
+// domain is tabulated once per proposal in shared memory; L is symmetric, so
+// row l keeps only the entries at columns l .. l + 64 (mod 128), 66 words
+// per row, which also makes the lookups of a warp (32 rows, one column)
+// fall into 32 different banks.  A growing domain changes L every step; it
+// is then computed on the fly.
+//
+// Accumulation order.  The tensor core rounds each MMA's sum toward zero, a
+// bias of about 0.72 * 2^-24 of the accumulator per MMA that compounds over
+// the chain.  Each stage therefore issues the small correction products
+// (hi*lo, lo*hi) first, while the accumulator is small, and the 8 main
+// products (hi*hi) last; the remaining shrink of about 8 * 0.5 * 2^-24 (the
+// partial sums average about 0.7 of the final value) is compensated by
+// multiplying each stage's output by 1 + 2^-22.
+//
+// TMEM (512 columns): 8C hi | 8C lo | 8C^T hi | 8C^T lo (64 columns each,
+// two FP16 per column) | field u accumulator | field v accumulator.
+// One 128^2 proposal per CTA, 544 threads: warps 0-7 convert field u,
+// 8-15 field v (two warps per TMEM lane quadrant), warp 16 allocates TMEM
+// and issues the MMAs.  Shared memory: the four operand tiles (u hi, u lo,
+// v hi, v lo; 32 KB each), the two L tables (33 KB each), control.
+// Bounded waits as in rd_solve_tc.cu.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "rd_common.cuh"
+#include "rd_internal.h"
+#include "rd_tc_ptx.cuh"
+
+namespace rd {
+
+using namespace tc;
+
+namespace tc2 {
+
+constexpr int N = 128;
+constexpr uint32_t kColCHi = 0, kColCLo = 64, kColCtHi = 128, kColCtLo = 192;
+constexpr uint32_t kColAcc = 256;  // + 128 f
+constexpr uint32_t kTileBytes = 128 * 128 * 2;  // one FP16 operand tile
+constexpr int kLamRow = 66;                     // words per L table row
+constexpr uint32_t kLamBytes = N * kLamRow * 4;
+constexpr uint32_t kOffLam = 4 * kTileBytes;    // after the tiles u hi, u lo, v hi, v lo
+constexpr uint32_t kOffCtrl = kOffLam + 2 * kLamBytes;
+constexpr uint32_t kSmemBytes = 1024 + kOffCtrl + 4096;
+// stage output scales with the round-toward-zero compensation 1 + 2^-22
+constexpr float kScale1 = 0x1p-7f + 0x1p-29f;   // stage 1: (1/128)(1 + 2^-22)
+constexpr float kScaleL = 0x1p-6f + 0x1p-28f;   // stage 2: L (1/64)(1 + 2^-22)
+constexpr float kScale3 = 1.f + 0x1p-22f;       // stage 3
+constexpr float kScaleW = 0x1p-7f + 0x1p-29f;   // stage 4 (state read): (1/128)(1 + 2^-22)
+
+struct Ctrl {
+  uint64_t mma_done[2];   // per field: its stage's MMAs completed
+  uint64_t op_half0[2];   // per field: first half of the stage-3 operand written
+  uint64_t op_all[2];     // per field: the whole next operand written
+  uint64_t rx_ready;      // reaction written (both fields)
+  uint64_t st_ready;      // both fields' stage 4 observed
+  uint64_t fin;
+  uint32_t tmem_base;
+  int abort;
+  int item;
+  int size;
+  int bad;
+  double phi;
+  double th[5];
+  float mu[N];
+};
+
+__device__ __forceinline__ uint8_t* tile(uint8_t* base, int f, int hl) {
+  return base + (uint32_t)(2 * f + hl) * kTileBytes;
+}
+
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// K-major stage (1, 2, 4) of field f: the correction products of all K
+// blocks first, then the main products.
+__device__ __forceinline__ void issue_kmajor(uint8_t* base, uint32_t tmem, int stage, int f) {
+  constexpr uint32_t idesc = idesc_f16_f32(128, N, 0, 0);
+  const uint32_t a_hi = tmem + (stage <= 2 ? kColCHi : kColCtHi);
+  const uint32_t a_lo = tmem + (stage <= 2 ? kColCLo : kColCtLo);
+  const uint64_t bh = sdesc_sw128(smem_u32(tile(base, f, 0)), 16u, 1024u);
+  const uint64_t bl = sdesc_sw128(smem_u32(tile(base, f, 1)), 16u, 1024u);
+  const uint32_t d = tmem + kColAcc + (uint32_t)(128 * f);
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const uint64_t off = ((uint32_t)(kk >> 2) * 16384u + (uint32_t)(kk & 3) * 32u) >> 4;
+    mma_ts(d, a_hi + (uint32_t)(kk * 8), bl + off, idesc, kk > 0 ? 1u : 0u);
+    mma_ts(d, a_lo + (uint32_t)(kk * 8), bh + off, idesc, 1u);
+  }
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const uint64_t off = ((uint32_t)(kk >> 2) * 16384u + (uint32_t)(kk & 3) * 32u) >> 4;
+    mma_ts(d, a_hi + (uint32_t)(kk * 8), bh + off, idesc, 1u);
+  }
+}
+
+// Stage 3 of field f, output columns [64 h, 64 h + 64): B = columns of the
+// MN-major operand tile in 64-column block h, all 128 K rows.
+__device__ __forceinline__ void issue_stage3(uint8_t* base, uint32_t tmem, int f, int h) {
+  constexpr uint32_t idesc = idesc_f16_f32(128, 64, 0, 1);
+  const uint32_t a_hi = tmem + kColCtHi, a_lo = tmem + kColCtLo;
+  const uint32_t boff = (uint32_t)h * 16384u;
+  const uint64_t bh = sdesc_sw128(smem_u32(tile(base, f, 0)) + boff, 16384u, 1024u);
+  const uint64_t bl = sdesc_sw128(smem_u32(tile(base, f, 1)) + boff, 16384u, 1024u);
+  const uint32_t d = tmem + kColAcc + (uint32_t)(128 * f + 64 * h);
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const uint64_t off = ((uint32_t)kk * 2048u) >> 4;
+    mma_ts(d, a_hi + (uint32_t)(kk * 8), bl + off, idesc, kk > 0 ? 1u : 0u);
+    mma_ts(d, a_lo + (uint32_t)(kk * 8), bh + off, idesc, 1u);
+  }
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const uint64_t off = ((uint32_t)kk * 2048u) >> 4;
+    mma_ts(d, a_hi + (uint32_t)(kk * 8), bh + off, idesc, 1u);
+  }
+}
+
+// L (with its scale) at row l, column c from the half table of a field.
+__device__ __forceinline__ float lam_at(const float* tab, int l, int c) {
+  const int d = (c - l) & (N - 1);
+  return d <= N / 2 ? tab[l * kLamRow + d] : tab[c * kLamRow + N - d];
+}
+
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
+  return (uint32_t)__half_as_ushort(__low2half(h)) |
+         ((uint32_t)__half_as_ushort(__high2half(h)) << 16);
+}
+
+// Splits 8 values (times scale) of row r, columns c..c+7 into the hi and lo
+// tiles: one 16-byte store each.
+__device__ __forceinline__ void store8(uint8_t* hi, uint8_t* lo, int r, int c, const float* x,
+                                       float scale) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __half2 hh, ll;
+    split_f16x2(x[2 * j] * scale, x[2 * j + 1] * scale, hh, ll);
+    h[j] = h2_bits(hh);
+    l[j] = h2_bits(ll);
+  }
+  const uint32_t off = sw128_offset(128, r, c);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Explicit reaction in place on 8 points: state (x 128) -> r_u, r_v deviations.
+__device__ __forceinline__ void react8(float* u, float* v, float sw, float ref_u, float ref_v,
+                                       float fa, float fb, float ftg, float cu, float cv) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float du = u[j] * sw, dv = v[j] * sw;
+    const float uu = ref_u + du, vv = ref_v + dv;
+    const float u2v = uu * uu * vv;
+    u[j] = fmaf(ftg, fa - uu + u2v, du) + cu;
+    v[j] = fmaf(ftg, fb - u2v, dv) + cv;
+  }
+}
+
+struct ObsCtx {
+  const float* yo;  // this observation's data, or null
+  float* fo;        // this proposal's output fields, or null
+  bool odd;         // state transposed (x on the lanes)
+};
+
+// Observation misfit and final-field output of 8 points of row l, columns c..c+7.
+__device__ __forceinline__ void observe8(const DevProblem& pb, const DevSize& S, const ObsCtx& o,
+                                         int l, int c, const float* u, const float* v, float sw,
+                                         double& phi, int& bad) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const size_t pt = o.odd ? (size_t)(c + j) * N + l : (size_t)l * N + c + j;  // y N + x
+    const float du = u[j] * sw, dv = v[j] * sw;
+    if (o.yo) {
+      int k = 0;
+      if (S.field_mask & 1) {
+        const double w = (double)S.ref_u + (double)du;
+        if (!(fabs(w) <= pb.w_max)) bad = 1;
+        const double e = (double)o.yo[pt] - w;
+        phi += e * e;
+        ++k;
+      }
+      if (S.field_mask & 2) {
+        const double w = (double)S.ref_v + (double)dv;
+        if (!(fabs(w) <= pb.w_max)) bad = 1;
+        const double e = (double)o.yo[(size_t)k * S.npts + pt] - w;
+        phi += e * e;
+      }
+    }
+    if (o.fo) {
+      o.fo[pt] = S.ref_u + du;
+      o.fo[(size_t)S.npts + pt] = S.ref_v + dv;
+    }
+  }
+}
+
+// One converter warp w (0 .. 8 WPF - 1), WPF warps per TMEM lane quadrant
+// and field.  Stage conversions: field f = w / (4 WPF), columns
+// [cw r, cw (r + 1)) of each half, cw = 64 / WPF, r = (w / 4) % WPF.
+// Reaction: both fields at columns [xw p, xw (p + 1)) of each half,
+// xw = 32 / WPF, p = w / 4.
+template <int WPF>
+__device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uint8_t* base,
+                          uint32_t tmem, int warp, int lane, uint32_t& ph_done, uint32_t& ph_st,
+                          float* fields, size_t field_stride) {
+  constexpr int CW = 64 / WPF;  // stage-conversion columns per half
+  constexpr int XW = 32 / WPF;  // reaction columns per half
+  volatile int* abort = &ctl->abort;
+  const int f = warp / (4 * WPF);
+  const int q = warp & 3;
+  const int rr = (warp >> 2) % WPF;
+  const int p = warp >> 2;
+  const int l = 32 * q + lane;
+  const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+  const uint32_t t_u = tmem + lane_off + kColAcc, t_v = t_u + 128u;
+  const uint32_t t_f = f ? t_v : t_u;
+  uint8_t* const hi_u = tile(base, 0, 0);
+  uint8_t* const lo_u = tile(base, 0, 1);
+  uint8_t* const hi_v = tile(base, 1, 0);
+  uint8_t* const lo_v = tile(base, 1, 1);
+  uint8_t* const hi_f = f ? hi_v : hi_u;
+  uint8_t* const lo_f = f ? lo_v : lo_u;
+  const float* lam_f = reinterpret_cast<const float*>(base + kOffLam + (uint32_t)f * kLamBytes);
+  const double* th = ctl->th;
+  const double tau = pb.tau;
+  const float fa = (float)th[0], fb = (float)th[1], ftg = (float)(tau * th[3]);
+  const double r = th[4];
+  const float ref_u = S.ref_u, ref_v = S.ref_v;
+  const int nfo = (S.field_mask & 1) + ((S.field_mask >> 1) & 1);
+  const float mu_l = ctl->mu[l];
+  double phi = 0.0;
+  int bad = 0;
+  int next_obs = 0;
+  for (int step = 0;; ++step) {
+    if (step > 0) {
+      if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
+      ++ph_done;
+      tc_fence_after();
+      mbar_arrive(&ctl->st_ready);
+      if (!mbar_wait_bounded(&ctl->st_ready, ph_st & 1u, abort)) return false;
+      ++ph_st;
+      tc_fence_after();
+    }
+    const bool last = step == pb.n_steps;
+    const float sw = step > 0 ? kScaleW : 0x1p-7f;
+    const bool obs = next_obs < S.n_obs && step == S.obs_steps[next_obs];
+    ObsCtx o;
+    o.yo = obs ? S.yf + (size_t)next_obs * nfo * S.npts : nullptr;
+    o.fo = (last && fields) ? fields + (size_t)ctl->item * field_stride : nullptr;
+    o.odd = step & 1;
+    if (obs) ++next_obs;
+    float alpha = 1.f, cu = 0.f, cv = 0.f;
+    float beta_f = 0.f;
+    if (pb.growth) {  // FP64, rounded once per step
+      const double rho2inv = exp(-2.0 * r * (double)step * tau);
+      alpha = (float)(1.0 + tau * 2.0 * r);
+      cu = (float)(-tau * 2.0 * r * (double)ref_u);
+      cv = (float)(-tau * 2.0 * r * (double)ref_v);
+      beta_f = (float)(tau * (f ? th[2] : 1.0) * rho2inv * (double)N * N);
+    }
+    // ---- observation / output, then the reaction -> stage-1 operands
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      const int x0 = 64 * half + XW * p;
+#pragma unroll
+      for (int j = 0; j < XW; j += 8) {
+        float u8[8], v8[8];
+        __syncwarp();
+        tmem_ld8(t_u + (uint32_t)(x0 + j), u8);
+        tmem_ld8(t_v + (uint32_t)(x0 + j), v8);
+        tmem_wait_ld();
+        if (o.yo || o.fo) observe8(pb, S, o, l, x0 + j, u8, v8, sw, phi, bad);
+        if (last) continue;
+        react8(u8, v8, sw, ref_u, ref_v, fa, fb, ftg, cu, cv);
+        store8(hi_u, lo_u, l, x0 + j, u8, 256.f);
+        store8(hi_v, lo_v, l, x0 + j, v8, 256.f);
+      }
+    }
+    if (last) break;
+    fence_proxy_async_smem();
+    tc_fence_before();
+    mbar_arrive(&ctl->rx_ready);
+
+    // ---- stages 1-3 of field f -> operands of stages 2-4
+#pragma unroll 1
+    for (int stage = 1; stage <= 3; ++stage) {
+      if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
+      ++ph_done;
+      tc_fence_after();
+      const float sc = stage == 1 ? kScale1 : stage == 3 ? kScale3 : 1.f;
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        const int c0 = 64 * half + CW * rr;
+#pragma unroll
+        for (int j = 0; j < CW; j += 32) {
+          float a[32];
+          __syncwarp();
+          tmem_ld32(t_f + (uint32_t)(c0 + j), a);
+          tmem_wait_ld();
+          if (stage == 2) {
+            if (pb.growth) {
+#pragma unroll
+              for (int k = 0; k < 32; ++k)
+                a[k] *= kScaleL * recip_nr(fmaf(beta_f, mu_l + ctl->mu[c0 + j + k], alpha));
+            } else {
+#pragma unroll
+              for (int k = 0; k < 32; ++k) a[k] *= lam_at(lam_f, l, c0 + j + k);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 32; k += 8) store8(hi_f, lo_f, l, c0 + j + k, a + k, sc);
+        }
+        if (stage == 2 && half == 0) {  // stage 3 starts on its first N half
+          fence_proxy_async_smem();
+          tc_fence_before();
+          mbar_arrive(&ctl->op_half0[f]);
+        }
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      mbar_arrive(&ctl->op_all[f]);
+    }
+  }
+  atomicAdd(&ctl->phi, phi);
+  if (bad) atomicOr(&ctl->bad, 1);
+  return true;
+}
+
+__device__ bool issuer(const DevProblem& pb, Ctrl* ctl, uint8_t* base, uint32_t tmem, int lane,
+                       uint32_t& ph_rx, uint32_t (&ph_h0)[2], uint32_t (&ph_all)[2]) {
+  volatile int* abort = &ctl->abort;
+  for (int step = 0; step < pb.n_steps; ++step) {
+    if (!mbar_wait_bounded(&ctl->rx_ready, ph_rx & 1u, abort)) return false;
+    ++ph_rx;
+    tc_fence_after();
+    if (lane == 0) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        issue_kmajor(base, tmem, 1, f);
+        mma_commit(&ctl->mma_done[f]);
+      }
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int stage = 2; stage <= 4; ++stage) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        if (stage == 3) {
+          if (!mbar_wait_bounded(&ctl->op_half0[f], ph_h0[f] & 1u, abort)) return false;
+          ++ph_h0[f];
+          tc_fence_after();
+          if (lane == 0) issue_stage3(base, tmem, f, 0);
+          __syncwarp();
+        }
+        if (!mbar_wait_bounded(&ctl->op_all[f], ph_all[f] & 1u, abort)) return false;
+        ++ph_all[f];
+        tc_fence_after();
+        if (lane == 0) {
+          if (stage == 3)
+            issue_stage3(base, tmem, f, 1);
+          else
+            issue_kmajor(base, tmem, stage, f);
+          mma_commit(&ctl->mma_done[f]);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  return true;
+}
+
+}  // namespace tc2
+
+template <int WPF>
+__global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
+    k_solve2d_tc128(DevProblem pb, WorkQueue q, const double* theta, double* phi,
+                    uint32_t* status, float* fields, size_t field_stride, int* err) {
+  using namespace tc2;
+  constexpr int kConvWarps = 8 * WPF;
+  constexpr int kThreads = 32 * (kConvWarps + 1);
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned start, derived from smem_raw so that the compiler keeps
+  // the shared address space (plain shared loads and stores, not generic)
+  uint8_t* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  Ctrl* ctl = reinterpret_cast<Ctrl*>(base + kOffCtrl);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == kConvWarps) {
+    tmem_alloc(&ctl->tmem_base, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int f = 0; f < 2; ++f) {
+      mbar_init(&ctl->mma_done[f], 1);
+      mbar_init(&ctl->op_half0[f], 32 * kConvWarps / 2);
+      mbar_init(&ctl->op_all[f], 32 * kConvWarps / 2);
+    }
+    mbar_init(&ctl->rx_ready, 32 * kConvWarps);
+    mbar_init(&ctl->st_ready, 32 * kConvWarps);
+    mbar_init(&ctl->fin, 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+  // every size in this kernel's queue is 128^2: one DCT matrix serves all
+  const DevSize& S0 = pb.sz[q.order[0]];
+  // 8C and 8C^T as split FP16 into TMEM (lane = output index), once per CTA:
+  // the first half of the converter warps C, the second C^T
+  if (warp < kConvWarps) {
+    const bool tr = warp >= 4 * WPF;
+    const int m = 32 * (warp & 3) + lane;
+    const int cbase = (64 / WPF) * ((warp >> 2) % WPF);
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    for (int c0 = cbase; c0 < cbase + 64 / WPF; c0 += 8) {
+      float vh[8], vl[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k0 = 2 * (c0 + j), k1 = k0 + 1;
+        const float e0 = 8.f * (tr ? S0.cmat[(size_t)k0 * N + m] : S0.cmat[(size_t)m * N + k0]);
+        const float e1 = 8.f * (tr ? S0.cmat[(size_t)k1 * N + m] : S0.cmat[(size_t)m * N + k1]);
+        __half h0, l0, h1, l1;
+        split_f16(e0, h0, l0);
+        split_f16(e1, h1, l1);
+        vh[j] = __uint_as_float((uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16));
+        vl[j] = __uint_as_float((uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16));
+      }
+      __syncwarp();
+      tmem_st8(tmem + lane_off + (tr ? kColCtHi : kColCHi) + (uint32_t)c0, vh);
+      tmem_st8(tmem + lane_off + (tr ? kColCtLo : kColCLo) + (uint32_t)c0, vl);
+    }
+    tmem_wait_st();
+  }
+  for (int i = tid; i < N; i += kThreads) ctl->mu[i] = S0.mu[i];
+  uint32_t ph_done = 0, ph_st = 0, ph_rx = 0;
+  uint32_t ph_h0[2] = {0, 0}, ph_all[2] = {0, 0};
+  for (;;) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      int sz = 0;
+      ctl->item = ctl->abort ? -1 : queue_pop(q, &sz);
+      ctl->size = sz;
+      if (ctl->item >= 0) full_theta(pb, theta + (size_t)ctl->item * pb.n_params, ctl->th);
+      ctl->phi = 0.0;
+      ctl->bad = 0;
+    }
+    __syncthreads();
+    if (ctl->item < 0) break;
+    const DevSize& S = pb.sz[ctl->size];
+    if (warp < kConvWarps) {  // initial deviations (x 128), y on the lanes
+      const int l = 32 * (warp & 3) + lane;
+      const int p = warp >> 2;
+      const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+      for (int f = 0; f < 2; ++f) {
+        const float ref = f ? S.ref_v : S.ref_u;
+        const float* w0 = f ? S.v0f : S.u0f;
+        for (int x = (32 / WPF) * p; x < N; x += 64) {
+#pragma unroll
+          for (int x8 = 0; x8 < 32 / WPF; x8 += 8) {
+            float v8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v8[j] = (w0[(size_t)l * N + x + x8 + j] - ref) * 128.f;
+            __syncwarp();
+            tmem_st8(tmem + lane_off + kColAcc + (uint32_t)(128 * f + x + x8), v8);
+          }
+        }
+      }
+      tmem_wait_st();
+      if (!pb.growth) {  // L tables of this proposal (both fields)
+        float* lam = reinterpret_cast<float*>(base + kOffLam);
+        for (int i = tid; i < 2 * N * (N / 2 + 1); i += 32 * kConvWarps) {
+          const int f = i / (N * (N / 2 + 1));
+          const int rem = i - f * (N * (N / 2 + 1));
+          const int row = rem / (N / 2 + 1), d = rem - row * (N / 2 + 1);
+          const float beta = (float)(pb.tau * (f ? ctl->th[2] : 1.0) * (double)N * N);
+          const float mur = ctl->mu[row], muc = ctl->mu[(row + d) & (N - 1)];
+          lam[f * N * kLamRow + row * kLamRow + d] = kScaleL / fmaf(beta, mur + muc, 1.f);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp < kConvWarps)
+      converter<WPF>(pb, S, ctl, base, tmem, warp, lane, ph_done, ph_st, fields, field_stride);
+    else
+      issuer(pb, ctl, base, tmem, lane, ph_rx, ph_h0, ph_all);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && !ctl->abort) {
+      const int b = ctl->item;
+      status[b] = ctl->bad ? (uint32_t)RD_P_NONFINITE : 0u;
+      phi[b] = ctl->bad ? (double)INFINITY : ctl->phi * S.inv_two_sigma2;
+    }
+  }
+  if (warp == kConvWarps) {
+    if (lane == 0) mma_commit(&ctl->fin);
+    __syncwarp();
+    volatile int never = 0;
+    mbar_wait_bounded(&ctl->fin, 0, &never);
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+  if (tid == 0 && ctl->abort) atomicOr(err, 1);
+}
+
+bool tc128_applicable(const DevProblem& pb, int size_idx) {
+  return pb.dim == 2 && pb.sz[size_idx].n == 128;
+}
+
+// Converter warps per TMEM lane quadrant and field.
+constexpr int kTc128Wpf = 2;
+
+cudaError_t setup_solve_tc128() {
+  return cudaFuncSetAttribute(k_solve2d_tc128<kTc128Wpf>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::kSmemBytes);
+}
+
+int grid_solve_tc128(int n_sm) { return n_sm; }
+
+cudaError_t launch_solve_tc128(const DevProblem& pb, const WorkQueue& q, const double* theta,
+                               double* phi, uint32_t* status, void* fields, int grid, int* err,
+                               cudaStream_t st) {
+  const size_t stride = (size_t)2 * pb.max_n * pb.max_n;
+  k_solve2d_tc128<kTc128Wpf><<<grid, 32 * (8 * kTc128Wpf + 1), tc2::kSmemBytes, st>>>(
+      pb, q, theta, phi, status, (float*)fields, stride, err);
+  return cudaGetLastError();
+}
+
+}  // namespace rd
