@@ -189,6 +189,21 @@ rd_status rd_set_size_kernel(rd_problem* p, int size_idx, int kernel);
 /* The kernel size `size_idx` runs with, RD_KERNEL_DEFAULT resolved. */
 rd_status rd_get_size_kernel(const rd_problem* p, int size_idx, int* kernel);
 
+/* Timed search of the solve kernel of every grid size of a 2-D problem:
+ * for each size s, solves the B proposals theta (host, [B][n_params], the
+ * same batch for every candidate) as size s with each kernel that supports
+ * it, one warm-up and n_trials timed launches (CUDA events on the problem's
+ * stream), probe_steps IMEX steps per solve (0 = the problem's n_steps), and
+ * sets the kernel with the lowest median time (rd_set_size_kernel).  Sizes
+ * of a problem run one persistent launch per kernel kind, so the choice per
+ * size stays within one batched evaluation.  times_out (host, may be NULL):
+ * [n_sizes][3] seconds per proposal for RD_KERNEL_SIMT, TC_STACKED and
+ * TC_RESIDENT, NaN where a kernel does not apply.  Allocates scratch for the
+ * batch; synchronises the stream.  EINVAL for a 1-D problem; on a failed
+ * launch the previous choices are kept. */
+rd_status rd_autotune(rd_problem* p, int B, const double* theta, int n_trials, int probe_steps,
+                      double* times_out);
+
 /* Chains: n_chains independent random-walk Metropolis chains advanced in
  * lock-step, one proposal per chain per step (Algorithm 1).
  * theta0:   host [C][n_params] starting points

@@ -42,7 +42,7 @@ EXPORTS = (
     "rd_surrogate_create", "rd_surrogate_destroy", "rd_surrogate_train",
     "rd_surrogate_predict", "rd_surrogate_loss_grad", "rd_surrogate_get_params",
     "rd_surrogate_set_params", "rd_chains_set_surrogate", "rd_chains_set_proposal",
-    "rd_set_size_kernel", "rd_get_size_kernel",
+    "rd_set_size_kernel", "rd_get_size_kernel", "rd_autotune",
 )
 
 
@@ -229,6 +229,17 @@ def rd_get_size_kernel(p, size_idx):
     k = ctypes.c_int(0)
     _check(load().rd_get_size_kernel(p, size_idx, ctypes.byref(k)))
     return k.value
+
+
+def rd_autotune(p, theta, n_trials=3, probe_steps=0, n_sizes=None):
+    """theta: host [B][P].  Returns [n_sizes][3] seconds per proposal (SIMT,
+    TC_STACKED, TC_RESIDENT; NaN where not applicable)."""
+    th, pt = _host_ptr(theta, np.float64)
+    ns = n_sizes if n_sizes is not None else RD_MAX_SIZES
+    out = np.full((RD_MAX_SIZES, 3), np.nan)
+    _check(load().rd_autotune(p, th.shape[0], pt, n_trials, probe_steps,
+                              out.ctypes.data_as(ctypes.c_void_p)))
+    return out[:ns]
 
 
 def rd_evaluate_batch_host(p, theta, size_idx=None):

@@ -456,6 +456,97 @@ rd_status rd_sync(rd_problem* p) {
   return RD_OK;
 }
 
+// ------------------------------------------------------------------ autotuning
+rd_status rd_autotune(rd_problem* p, int B, const double* theta, int n_trials, int probe_steps,
+                      double* times_out) {
+  RD_CHECK(p && theta, RD_EINVAL, "NULL argument");
+  RD_CHECK(p->desc.dim == 2, RD_EINVAL, "autotuning applies to 2-D problems");
+  RD_CHECK(B > 0 && n_trials > 0 && probe_steps >= 0, RD_EINVAL,
+           "B and n_trials must be > 0, probe_steps >= 0");
+  rd_status r = check_ready(p);
+  if (r != RD_OK) return r;
+  if ((r = ensure_capacity(p, B)) != RD_OK) return r;
+  const int P = p->desc.n_params, ns = p->desc.n_sizes;
+  static const int kinds[3] = {RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT};
+  double times[RD_MAX_SIZES][3];
+  double* d_theta = nullptr;
+  double* d_phi = nullptr;
+  uint32_t* d_st = nullptr;
+  int* d_size = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int saved_steps = p->dev.n_steps;
+  int saved_kernel[RD_MAX_SIZES];
+  for (int s = 0; s < RD_MAX_SIZES; ++s) saved_kernel[s] = p->kernel_of_size[s];
+  std::string fail;
+  auto cu = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && fail.empty()) fail = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaSuccess;
+  };
+  bool ok = cu(cudaMalloc(&d_theta, sizeof(double) * (size_t)B * P), "cudaMalloc") &&
+            cu(cudaMalloc(&d_phi, sizeof(double) * (size_t)B), "cudaMalloc") &&
+            cu(cudaMalloc(&d_st, sizeof(uint32_t) * (size_t)B), "cudaMalloc") &&
+            cu(cudaMalloc(&d_size, sizeof(int) * (size_t)B), "cudaMalloc") &&
+            cu(cudaEventCreate(&e0), "cudaEventCreate") &&
+            cu(cudaEventCreate(&e1), "cudaEventCreate") &&
+            cu(cudaMemcpyAsync(d_theta, theta, sizeof(double) * (size_t)B * P,
+                               cudaMemcpyHostToDevice, p->stream), "cudaMemcpyAsync");
+  if (ok && probe_steps > 0 && probe_steps < saved_steps) p->dev.n_steps = probe_steps;
+  std::vector<int> sizes((size_t)B);
+  for (int s = 0; ok && s < ns; ++s) {
+    std::fill(sizes.begin(), sizes.end(), s);
+    ok = cu(cudaMemcpyAsync(d_size, sizes.data(), sizeof(int) * (size_t)B, cudaMemcpyHostToDevice,
+                            p->stream), "cudaMemcpyAsync") &&
+         cu(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    int best = -1;
+    for (int k = 0; ok && k < 3; ++k) {
+      times[s][k] = NAN;
+      if (kinds[k] == RD_KERNEL_TC_RESIDENT && p->desc.nx[s] != 128) continue;
+      p->kernel_of_size[s] = kinds[k];
+      std::vector<float> ms;
+      for (int t = 0; ok && t <= n_trials; ++t) {  // trial 0 warms up
+        const WorkQueue q = make_queue(p);
+        ok = cu(cudaEventRecord(e0, p->stream), "cudaEventRecord") &&
+             cu(launch_fill_queue(q, B, d_size, d_phi, d_st, p->stream), "fill") &&
+             cu(launch_solve(p, d_theta, d_phi, d_st, nullptr), "solve") &&
+             cu(cudaEventRecord(e1, p->stream), "cudaEventRecord") &&
+             cu(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float m = 0.f;
+        if (ok && t > 0 && cu(cudaEventElapsedTime(&m, e0, e1), "cudaEventElapsedTime"))
+          ms.push_back(m);
+      }
+      int err = 0;
+      if (ok) ok = cu(cudaMemcpy(&err, p->ws.err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+      if (ok && err) {
+        cudaMemset(p->ws.err, 0, sizeof(int));
+        fail = "a solve kernel's bounded wait gave up during autotuning";
+        ok = false;
+      }
+      if (!ok) break;
+      std::sort(ms.begin(), ms.end());
+      times[s][k] = 1e-3 * (double)ms[ms.size() / 2] / B;  // seconds per proposal
+      if (best < 0 || times[s][k] < times[s][best]) best = k;
+    }
+    if (ok) saved_kernel[s] = kinds[best];
+  }
+  p->dev.n_steps = saved_steps;
+  for (int s = 0; s < RD_MAX_SIZES; ++s) p->kernel_of_size[s] = saved_kernel[s];
+  ++p->generation;  // captured chain steps hold the old launches
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d_theta);
+  cudaFree(d_phi);
+  cudaFree(d_st);
+  cudaFree(d_size);
+  if (!ok) {
+    set_error("rd_autotune: " + fail);
+    return fail.find("bounded wait") != std::string::npos ? RD_ETIMEOUT : RD_ECUDA;
+  }
+  if (times_out)
+    for (int s = 0; s < ns; ++s)
+      for (int k = 0; k < 3; ++k) times_out[3 * s + k] = times[s][k];
+  return RD_OK;
+}
+
 // ------------------------------------------------------------------ chains
 rd_status rd_chains_destroy(rd_chains* c) {
   if (!c) return RD_OK;
