@@ -156,23 +156,13 @@ __device__ __forceinline__ float lam_at(const float* tab, int l, int c) {
   return d <= N / 2 ? tab[l * kLamRow + d] : tab[c * kLamRow + N - d];
 }
 
-__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
-  return (uint32_t)__half_as_ushort(__low2half(h)) |
-         ((uint32_t)__half_as_ushort(__high2half(h)) << 16);
-}
-
 // Splits 8 values (times scale) of row r, columns c..c+7 into the hi and lo
 // tiles: one 16-byte store each.
 __device__ __forceinline__ void store8(uint8_t* hi, uint8_t* lo, int r, int c, const float* x,
                                        float scale) {
   uint32_t h[4], l[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    __half2 hh, ll;
-    split_f16x2(x[2 * j] * scale, x[2 * j + 1] * scale, hh, ll);
-    h[j] = h2_bits(hh);
-    l[j] = h2_bits(ll);
-  }
+  for (int j = 0; j < 4; ++j) split_f16x2_scaled(x[2 * j], x[2 * j + 1], scale, h[j], l[j]);
   const uint32_t off = sw128_offset(128, r, c);
   *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
@@ -296,18 +286,21 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
       const int x0 = 64 * half + XW * p;
+      float uh[XW], vh[XW];  // all loads of the half in flight at once
+      __syncwarp();
 #pragma unroll
       for (int j = 0; j < XW; j += 8) {
-        float u8[8], v8[8];
-        __syncwarp();
-        tmem_ld8(t_u + (uint32_t)(x0 + j), u8);
-        tmem_ld8(t_v + (uint32_t)(x0 + j), v8);
-        tmem_wait_ld();
-        if (o.yo || o.fo) observe8(pb, S, o, l, x0 + j, u8, v8, sw, phi, bad);
+        tmem_ld8(t_u + (uint32_t)(x0 + j), *reinterpret_cast<float(*)[8]>(uh + j));
+        tmem_ld8(t_v + (uint32_t)(x0 + j), *reinterpret_cast<float(*)[8]>(vh + j));
+      }
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < XW; j += 8) {
+        if (o.yo || o.fo) observe8(pb, S, o, l, x0 + j, uh + j, vh + j, sw, phi, bad);
         if (last) continue;
-        react8(u8, v8, sw, ref_u, ref_v, fa, fb, ftg, cu, cv);
-        store8(hi_u, lo_u, l, x0 + j, u8, 256.f);
-        store8(hi_v, lo_v, l, x0 + j, v8, 256.f);
+        react8(uh + j, vh + j, sw, ref_u, ref_v, fa, fb, ftg, cu, cv);
+        store8(hi_u, lo_u, l, x0 + j, uh + j, 256.f);
+        store8(hi_v, lo_v, l, x0 + j, vh + j, 256.f);
       }
     }
     if (last) break;

@@ -200,5 +200,29 @@ __device__ __forceinline__ void split_f16x2(float a, float b, __half2& hi, __hal
   lo = __floats2half2_rn(a - h.x, b - h.y);
 }
 
+// split_f16x2 of (a s, b s) with the FP32 arithmetic done on packed pairs:
+// hi = {fp16(a s), fp16(b s)} and lo = the rounded remainders, each as one
+// 32-bit word with the first value in the low half.  Same values as
+// split_f16x2(a * s, b * s).
+__device__ __forceinline__ void split_f16x2_scaled(float a, float b, float s, uint32_t& hi,
+                                                   uint32_t& lo) {
+  asm("{\n\t.reg .b64 x, y, r;\n\t.reg .f32 x0, x1, y0, y1, r0, r1;\n\t"
+      ".reg .b16 h0, h1;\n\t"
+      "mov.b64 x, {%2, %3};\n\t"
+      "mov.b64 y, {%4, %4};\n\t"
+      "mul.rn.f32x2 x, x, y;\n\t"
+      "mov.b64 {x0, x1}, x;\n\t"
+      "cvt.rn.f16x2.f32 %0, x1, x0;\n\t"
+      "mov.b32 {h0, h1}, %0;\n\t"
+      "cvt.f32.f16 y0, h0;\n\t"
+      "cvt.f32.f16 y1, h1;\n\t"
+      "mov.b64 y, {y0, y1};\n\t"
+      "sub.rn.f32x2 r, x, y;\n\t"
+      "mov.b64 {r0, r1}, r;\n\t"
+      "cvt.rn.f16x2.f32 %1, r1, r0;\n\t}"
+      : "=r"(hi), "=r"(lo)
+      : "f"(a), "f"(b), "f"(s));
+}
+
 }  // namespace tc
 }  // namespace rd
