@@ -25,12 +25,12 @@
 // N halves, so its first half starts while the second half of its operand
 // is still being written.
 //
-// The diagonal factor L (times 1/64 and the compensation below) of a fixed
-// domain is tabulated once per proposal in shared memory; L is symmetric, so
-// row l keeps only the entries at columns l .. l + 64 (mod 128), 66 words
-// per row, which also makes the lookups of a warp (32 rows, one column)
-// fall into 32 different banks.  A growing domain changes L every step; it
-// is then computed on the fly.
+// The diagonal factor L = 1 / (alpha + beta (mu_l + mu_k)) (times 1/64 and
+// the compensation below) is computed where it is applied: the reciprocal by
+// the hardware approximation plus one Newton-Raphson step, on pairs of
+// columns with the paired FP32 instructions.  The hi/lo operand split uses
+// the paired instructions too: the converter warps are instruction-bound,
+// and the tensor core waits on them.
 //
 // Accumulation order.  The tensor core rounds each MMA's sum toward zero, a
 // bias of about 0.72 * 2^-24 of the accumulator per MMA that compounds over
@@ -45,7 +45,7 @@
 // One 128^2 proposal per CTA, 544 threads: warps 0-7 convert field u,
 // 8-15 field v (two warps per TMEM lane quadrant), warp 16 allocates TMEM
 // and issues the MMAs.  Shared memory: the four operand tiles (u hi, u lo,
-// v hi, v lo; 32 KB each), the two L tables (33 KB each), control.
+// v hi, v lo; 32 KB each) and control.
 // Bounded waits as in rd_solve_tc.cu.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -65,10 +65,7 @@ constexpr int N = 128;
 constexpr uint32_t kColCHi = 0, kColCLo = 64, kColCtHi = 128, kColCtLo = 192;
 constexpr uint32_t kColAcc = 256;  // + 128 f
 constexpr uint32_t kTileBytes = 128 * 128 * 2;  // one FP16 operand tile
-constexpr int kLamRow = 66;                     // words per L table row
-constexpr uint32_t kLamBytes = N * kLamRow * 4;
-constexpr uint32_t kOffLam = 4 * kTileBytes;    // after the tiles u hi, u lo, v hi, v lo
-constexpr uint32_t kOffCtrl = kOffLam + 2 * kLamBytes;
+constexpr uint32_t kOffCtrl = 4 * kTileBytes;  // after the tiles u hi, u lo, v hi, v lo
 constexpr uint32_t kSmemBytes = 1024 + kOffCtrl + 4096;
 // stage output scales with the round-toward-zero compensation 1 + 2^-22
 constexpr float kScale1 = 0x1p-7f + 0x1p-29f;   // stage 1: (1/128)(1 + 2^-22)
@@ -150,12 +147,6 @@ __device__ __forceinline__ void issue_stage3(uint8_t* base, uint32_t tmem, int f
   }
 }
 
-// L (with its scale) at row l, column c from the half table of a field.
-__device__ __forceinline__ float lam_at(const float* tab, int l, int c) {
-  const int d = (c - l) & (N - 1);
-  return d <= N / 2 ? tab[l * kLamRow + d] : tab[c * kLamRow + N - d];
-}
-
 // Splits 8 values (times scale) of row r, columns c..c+7 into the hi and lo
 // tiles: one 16-byte store each.
 __device__ __forceinline__ void store8(uint8_t* hi, uint8_t* lo, int r, int c, const float* x,
@@ -168,7 +159,21 @@ __device__ __forceinline__ void store8(uint8_t* hi, uint8_t* lo, int r, int c, c
   *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Explicit reaction in place on 8 points: state (x 128) -> r_u, r_v deviations.
+// As store8 with one scale per value.
+__device__ __forceinline__ void store8s(uint8_t* hi, uint8_t* lo, int r, int c, const float* x,
+                                        const float* s8) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    split_f16x2_scaled2(x[2 * j], x[2 * j + 1], s8[2 * j], s8[2 * j + 1], h[j], l[j]);
+  const uint32_t off = sw128_offset(128, r, c);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Explicit reaction in place on 8 points: state (x 128) ->
+// r_u = du + tau gamma (a - u + u^2 v) (+ cu), r_v = dv + tau gamma (b - u^2 v)
+// (+ cv), as deviations from the reference state.
 __device__ __forceinline__ void react8(float* u, float* v, float sw, float ref_u, float ref_v,
                                        float fa, float fb, float ftg, float cu, float cv) {
 #pragma unroll
@@ -244,11 +249,11 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
   uint8_t* const lo_v = tile(base, 1, 1);
   uint8_t* const hi_f = f ? hi_v : hi_u;
   uint8_t* const lo_f = f ? lo_v : lo_u;
-  const float* lam_f = reinterpret_cast<const float*>(base + kOffLam + (uint32_t)f * kLamBytes);
   const double* th = ctl->th;
   const double tau = pb.tau;
   const float fa = (float)th[0], fb = (float)th[1], ftg = (float)(tau * th[3]);
   const double r = th[4];
+  const float beta_fixed = (float)(tau * (f ? th[2] : 1.0) * (double)N * N);
   const float ref_u = S.ref_u, ref_v = S.ref_v;
   const int nfo = (S.field_mask & 1) + ((S.field_mask >> 1) & 1);
   const float mu_l = ctl->mu[l];
@@ -274,7 +279,7 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
     o.odd = step & 1;
     if (obs) ++next_obs;
     float alpha = 1.f, cu = 0.f, cv = 0.f;
-    float beta_f = 0.f;
+    float beta_f = beta_fixed;
     if (pb.growth) {  // FP64, rounded once per step
       const double rho2inv = exp(-2.0 * r * (double)step * tau);
       alpha = (float)(1.0 + tau * 2.0 * r);
@@ -324,18 +329,24 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
           __syncwarp();
           tmem_ld32(t_f + (uint32_t)(c0 + j), a);
           tmem_wait_ld();
-          if (stage == 2) {
-            if (pb.growth) {
+          if (stage == 2) {  // S = D L, L from mu_l + mu_k two columns at a time
+            const uint64_t ml2 = f2_pack(mu_l, mu_l), be2 = f2_pack(beta_f, beta_f);
+            const uint64_t al2 = f2_pack(alpha, alpha), ks2 = f2_pack(kScaleL, kScaleL);
 #pragma unroll
-              for (int k = 0; k < 32; ++k)
-                a[k] *= kScaleL * recip_nr(fmaf(beta_f, mu_l + ctl->mu[c0 + j + k], alpha));
-            } else {
+            for (int k = 0; k < 32; k += 8) {
+              float lam8[8];
 #pragma unroll
-              for (int k = 0; k < 32; ++k) a[k] *= lam_at(lam_f, l, c0 + j + k);
+              for (int jj = 0; jj < 8; jj += 2) {
+                const float2 mc = *reinterpret_cast<const float2*>(&ctl->mu[c0 + j + k + jj]);
+                const uint64_t x2 = f2_fma(f2_add(ml2, f2_pack(mc.x, mc.y)), be2, al2);
+                f2_unpack(f2_mul(f2_recip_nr(x2), ks2), lam8[jj], lam8[jj + 1]);
+              }
+              store8s(hi_f, lo_f, l, c0 + j + k, a + k, lam8);
             }
-          }
+          } else {
 #pragma unroll
-          for (int k = 0; k < 32; k += 8) store8(hi_f, lo_f, l, c0 + j + k, a + k, sc);
+            for (int k = 0; k < 32; k += 8) store8(hi_f, lo_f, l, c0 + j + k, a + k, sc);
+          }
         }
         if (stage == 2 && half == 0) {  // stage 3 starts on its first N half
           fence_proxy_async_smem();
@@ -496,17 +507,6 @@ __global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
         }
       }
       tmem_wait_st();
-      if (!pb.growth) {  // L tables of this proposal (both fields)
-        float* lam = reinterpret_cast<float*>(base + kOffLam);
-        for (int i = tid; i < 2 * N * (N / 2 + 1); i += 32 * kConvWarps) {
-          const int f = i / (N * (N / 2 + 1));
-          const int rem = i - f * (N * (N / 2 + 1));
-          const int row = rem / (N / 2 + 1), d = rem - row * (N / 2 + 1);
-          const float beta = (float)(pb.tau * (f ? ctl->th[2] : 1.0) * (double)N * N);
-          const float mur = ctl->mu[row], muc = ctl->mu[(row + d) & (N - 1)];
-          lam[f * N * kLamRow + row * kLamRow + d] = kScaleL / fmaf(beta, mur + muc, 1.f);
-        }
-      }
     }
     tc_fence_before();
     __syncthreads();

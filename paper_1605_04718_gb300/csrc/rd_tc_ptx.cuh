@@ -200,16 +200,62 @@ __device__ __forceinline__ void split_f16x2(float a, float b, __half2& hi, __hal
   lo = __floats2half2_rn(a - h.x, b - h.y);
 }
 
-// split_f16x2 of (a s, b s) with the FP32 arithmetic done on packed pairs:
-// hi = {fp16(a s), fp16(b s)} and lo = the rounded remainders, each as one
-// 32-bit word with the first value in the low half.  Same values as
-// split_f16x2(a * s, b * s).
-__device__ __forceinline__ void split_f16x2_scaled(float a, float b, float s, uint32_t& hi,
-                                                   uint32_t& lo) {
+// ---------------------------------------------------------------- packed FP32
+// Two FP32 values in one 64-bit register (first value in the low half),
+// operated on by the paired FP32 instructions (add/sub/mul/fma .f32x2), each
+// element rounded to nearest as by the scalar instruction.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t x, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// a * b + c, one rounding per element
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// 1/x of both elements: the hardware approximation refined by one
+// Newton-Raphson step r' = r + r (1 - x r), as recip_nr.
+__device__ __forceinline__ uint64_t f2_recip_nr(uint64_t x) {
+  float x0, x1, r0, r1;
+  f2_unpack(x, x0, x1);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x0));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(x1));
+  const uint64_t r = f2_pack(r0, r1);
+  const uint64_t e = f2_fma(f2_sub(0ull, x), r, f2_pack(1.f, 1.f));
+  return f2_fma(r, e, r);
+}
+
+// hi = {fp16(a sa), fp16(b sb)} and lo = the rounded remainders
+// {fp16(a sa - hi_a), fp16(b sb - hi_b)}, each as one 32-bit word with the
+// first value in the low half: split_f16 of the two scaled values, with the
+// FP32 arithmetic done on the pair at once.
+__device__ __forceinline__ void split_f16x2_scaled2(float a, float b, float sa, float sb,
+                                                    uint32_t& hi, uint32_t& lo) {
   asm("{\n\t.reg .b64 x, y, r;\n\t.reg .f32 x0, x1, y0, y1, r0, r1;\n\t"
       ".reg .b16 h0, h1;\n\t"
       "mov.b64 x, {%2, %3};\n\t"
-      "mov.b64 y, {%4, %4};\n\t"
+      "mov.b64 y, {%4, %5};\n\t"
       "mul.rn.f32x2 x, x, y;\n\t"
       "mov.b64 {x0, x1}, x;\n\t"
       "cvt.rn.f16x2.f32 %0, x1, x0;\n\t"
@@ -221,7 +267,11 @@ __device__ __forceinline__ void split_f16x2_scaled(float a, float b, float s, ui
       "mov.b64 {r0, r1}, r;\n\t"
       "cvt.rn.f16x2.f32 %1, r1, r0;\n\t}"
       : "=r"(hi), "=r"(lo)
-      : "f"(a), "f"(b), "f"(s));
+      : "f"(a), "f"(b), "f"(sa), "f"(sb));
+}
+__device__ __forceinline__ void split_f16x2_scaled(float a, float b, float s, uint32_t& hi,
+                                                   uint32_t& lo) {
+  split_f16x2_scaled2(a, b, s, s, hi, lo);
 }
 
 }  // namespace tc
