@@ -27,8 +27,8 @@
 //
 // The diagonal factor L = 1 / (alpha + beta (mu_l + mu_k)) (times 1/64 and
 // the compensation below) is computed where it is applied: the reciprocal by
-// the hardware approximation plus one Newton-Raphson step, on pairs of
-// columns with the paired FP32 instructions.  The hi/lo operand split uses
+// the hardware approximation (within one ulp), on pairs of columns with the
+// paired FP32 instructions.  The hi/lo operand split uses
 // the paired instructions too: the converter warps are instruction-bound,
 // and the tensor core waits on them.
 //
@@ -339,7 +339,7 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
               for (int jj = 0; jj < 8; jj += 2) {
                 const float2 mc = *reinterpret_cast<const float2*>(&ctl->mu[c0 + j + k + jj]);
                 const uint64_t x2 = f2_fma(f2_add(ml2, f2_pack(mc.x, mc.y)), be2, al2);
-                f2_unpack(f2_mul(f2_recip_nr(x2), ks2), lam8[jj], lam8[jj + 1]);
+                f2_unpack(f2_mul(f2_recip(x2), ks2), lam8[jj], lam8[jj + 1]);
               }
               store8s(hi_f, lo_f, l, c0 + j + k, a + k, lam8);
             }

@@ -234,6 +234,16 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
   return r;
 }
 
+// 1/x of both elements: the hardware approximation (rcp.approx, at most one
+// ulp from the exact reciprocal).
+__device__ __forceinline__ uint64_t f2_recip(uint64_t x) {
+  float x0, x1, r0, r1;
+  f2_unpack(x, x0, x1);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x0));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(x1));
+  return f2_pack(r0, r1);
+}
+
 // 1/x of both elements: the hardware approximation refined by one
 // Newton-Raphson step r' = r + r (1 - x r), as recip_nr.
 __device__ __forceinline__ uint64_t f2_recip_nr(uint64_t x) {
