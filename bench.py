@@ -32,6 +32,31 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # RD_KERNEL_* of include/rdbayes.h
 KERNELS = {"simt": 1, "stacked": 2, "resident": 3}
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full launch
+# (4096 proposals x 8000 steps at 128^2) of a solve kernel, from one ncu
+# capture of that launch (profiles/); reported only while the SHA-256 of the
+# kernel's sources still matches the one the capture ran on, else null.
+TRAFFIC = {}
+TRAFFIC_SOURCES = {
+    "k_solve2d_tc128<2>": ["rd_solve_tc2.cu", "rd_tc_ptx.cuh", "rd_common.cuh"],
+}
+
+
+def sources_sha256(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, "paper_1605_04718_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_of(kernel):
+    t = TRAFFIC.get(kernel)
+    if t and kernel in TRAFFIC_SOURCES and t["sha256"] == sources_sha256(kernel):
+        return t["bytes"]
+    return None
+
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -276,6 +301,7 @@ def run_gpu(args):
 
     import paper_1605_04718_gb300 as rd
     from paper_1605_04718_gb300 import build as rdbuild
+    from paper_1605_04718_gb300 import shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,10 +331,14 @@ def run_gpu(args):
     rd.rd_set_initial_state(p, 0, ds["u0"].astype(np.float64), ds["v0"].astype(np.float64))
     rd.rd_set_observations(p, 0, ds["obs_steps"], spec["field_mask"],
                            ds["y"].astype(np.float64), spec["sigma"])
-    theta0 = rd_synth.chain_starts(TRUE4, C, seed=1000 + rank, rel=0.002)
+    # weak scaling: C chains per GPU, rank r runs chains [r C, (r + 1) C) of one
+    # run of C * world chains (same seed, global chain index in the counters)
+    first, count = shard.shard(C * world, world, rank)
+    theta0 = rd_synth.chain_starts(TRUE4, C * world, seed=1000, rel=0.002)[first:first + count]
     step = [2e-4, 2e-4, 5e-4, 5e-4]
     cap = args.warmup + args.steps + 1
-    chains = rd.rd_chains_create(p, theta0, 4242 + rank, step, capacity=cap)
+    chains = rd.rd_chains_create(p, theta0, 4242, step, capacity=cap)
+    rd.rd_chains_set_first_chain(chains, first)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -389,10 +419,10 @@ def run_gpu(args):
         else:
             achieved = flop_per_solve * C / k_dur / 1e12
             tpk = _find(pk, "bf16_tflops") or FALLBACK_PEAKS["bf16_tflops"]
+            kname = ("k_solve2d_tc128<2>" if kind == rd.RD_KERNEL_TC_RESIDENT
+                     else "k_solve2d_tc<128>")
             roof = {"bound": "tensor", "achieved": achieved, "peak": tpk, "unit": "TFLOP/s",
-                    "frac": achieved / tpk, "traffic": None,
-                    "kernel": ("k_solve2d_tc128<2>" if kind == rd.RD_KERNEL_TC_RESIDENT
-                               else "k_solve2d_tc<128>"),
+                    "frac": achieved / tpk, "traffic": traffic_of(kname), "kernel": kname,
                     "kernel_ms": 1e3 * k_dur, "peak_source": f"{pk_src} bf16 burst (= fp16 rate)"}
         hbm = _find(pk, "hbm_gbs", "hbm_GBps", "copy_gbs") or FALLBACK_PEAKS["hbm_gbs"]
         roof["hbm_equiv"] = {"gbs": bytes_per_solve * C / k_dur / 1e9, "peak_gbs": hbm,

@@ -225,6 +225,16 @@ rd_status rd_chains_destroy(rd_chains* c);
  * unchanged.  L = diag(step) is the sampler rd_chains_create sets up. */
 rd_status rd_chains_set_proposal(rd_chains* c, const double* L);
 
+/* Global index of this object's chain 0 in the random-number counters
+ * (default 0): chain i draws at step s from counters (first + i, s, 0|1, 0).
+ * Chains split over several objects -- one per GPU, each taking a contiguous
+ * range of a run's chains with first = the range's start and the same seed --
+ * then draw exactly the numbers the chains of one object of the total size
+ * would (Sec. 2.1: many independent chains, pooled afterwards).  Set it
+ * before the first rd_chains_run; it is not part of a checkpoint.  EINVAL if
+ * first + n_chains exceeds 2^32. */
+rd_status rd_chains_set_first_chain(rd_chains* c, uint32_t first);
+
 /* Advances every chain by n_steps (async; graph-replayed per step).
  * ESTATE if the sample buffer would overflow. */
 rd_status rd_chains_run(rd_chains* c, int n_steps);

@@ -75,6 +75,8 @@ def lib():
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.orc_chain_randoms.argtypes = [ctypes.c_uint64, ctypes.c_int,
                                         ctypes.c_uint32, dp, dp]
+        L.orc_chain_randoms_from.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                             ctypes.c_uint32, dp, dp]
         L.orc_solve1d_thomas.argtypes = [ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, dp, dp]
         L.orc_dct_matrix.argtypes = [ctypes.c_int, dp]
@@ -114,14 +116,15 @@ def philox4x32_10(ctr, key):
     return out
 
 
-def chain_randoms(seed: int, n_chains: int, step: int):
+def chain_randoms(seed: int, n_chains: int, step: int, first: int = 0):
     """Normals [C][6] and uniforms [C][2] of every chain at one MCMC step
-    (counters (chain, step, 0|1, 0), key = seed).  Pinned by moment and
-    distribution tests and by the Philox known-answer values."""
+    (counters (first + chain, step, 0|1, 0), key = seed; first is the global
+    index of chain 0 when chains are split over processes).  Pinned by moment
+    and distribution tests and by the Philox known-answer values."""
     normals = np.zeros((n_chains, 6))
     uniforms = np.zeros((n_chains, 2))
-    lib().orc_chain_randoms(ctypes.c_uint64(seed), n_chains, step,
-                            _dp(normals), _dp(uniforms))
+    lib().orc_chain_randoms_from(ctypes.c_uint64(seed), first, n_chains, step,
+                                 _dp(normals), _dp(uniforms))
     return normals, uniforms
 
 

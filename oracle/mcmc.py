@@ -118,11 +118,13 @@ class Chains:
     turns each step into a delayed-acceptance step.
     """
 
-    def __init__(self, model: Model, theta0, seed: int, phi_fn, surrogate=None):
+    def __init__(self, model: Model, theta0, seed: int, phi_fn, surrogate=None,
+                 first_chain: int = 0):
         self.model = model
         self.theta = np.array(np.atleast_2d(theta0), dtype=np.float64)
         self.C = self.theta.shape[0]
         self.seed = int(seed)
+        self.first_chain = int(first_chain)  # global index of chain 0 (sharded runs)
         self.phi_fn = phi_fn
         self.surrogate = surrogate
         self.step_index = 0
@@ -138,7 +140,7 @@ class Chains:
     def step(self):
         """One step of Algorithm 1 (or its delayed-acceptance form)."""
         m = self.model
-        xi, uu = chain_randoms(self.seed, self.C, self.step_index)
+        xi, uu = chain_randoms(self.seed, self.C, self.step_index, self.first_chain)
         if m.chol is not None:  # correlated Gaussian random walk, increment L xi
             eta_bar = m.to_eta(self.theta) + xi[:, : m.P] @ np.asarray(m.chol).T
         else:

@@ -42,7 +42,7 @@ EXPORTS = (
     "rd_surrogate_create", "rd_surrogate_destroy", "rd_surrogate_train",
     "rd_surrogate_predict", "rd_surrogate_loss_grad", "rd_surrogate_get_params",
     "rd_surrogate_set_params", "rd_chains_set_surrogate", "rd_chains_set_proposal",
-    "rd_set_size_kernel", "rd_get_size_kernel", "rd_autotune",
+    "rd_set_size_kernel", "rd_get_size_kernel", "rd_autotune", "rd_chains_set_first_chain",
 )
 
 
@@ -372,6 +372,11 @@ def rd_surrogate_set_params(s, params=None, norm=None):
 
 def rd_chains_set_surrogate(c, s):
     _check(load().rd_chains_set_surrogate(c, s))
+
+
+def rd_chains_set_first_chain(c, first):
+    """Global index of chain 0 in the random-number counters (sharded runs)."""
+    _check(load().rd_chains_set_first_chain(c, ctypes.c_uint32(first)))
 
 
 def rd_chains_set_proposal(c, L):

@@ -689,6 +689,15 @@ rd_status rd_chains_set_proposal(rd_chains* c, const double* L) {
   return RD_OK;
 }
 
+rd_status rd_chains_set_first_chain(rd_chains* c, uint32_t first) {
+  RD_CHECK(c, RD_EINVAL, "chains is NULL");
+  RD_CHECK((uint64_t)first + (uint64_t)c->C <= 0x100000000ull, RD_EINVAL,
+           "first + n_chains must fit the 32-bit chain counter");
+  c->first_chain = first;
+  c->graph_ready = false;  // captured kernels hold it by value
+  return RD_OK;
+}
+
 rd_status rd_chains_set_surrogate(rd_chains* c, rd_surrogate* s) {
   RD_CHECK(c, RD_EINVAL, "chains is NULL");
   RD_CUDA(cudaStreamSynchronize(c->pb->stream));

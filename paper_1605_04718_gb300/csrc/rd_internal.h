@@ -58,6 +58,7 @@ struct rd_chains {
   int C = 0;
   int P = 0;
   uint64_t seed = 0;
+  uint32_t first_chain = 0;  // global index of chain 0 in the Philox counters
   int capacity = 0;
   int ring_host = 0;  // samples in the device ring (host mirror)
   double step[RD_NPARAM] = {0, 0, 0, 0, 0};

@@ -25,6 +25,7 @@ namespace rd {
 struct ChainView {
   int C, P;
   uint64_t seed;
+  uint32_t first;  // global index of chain 0 in the Philox counters
   double chol[kNParam * kNParam];  // lower-triangular proposal factor
   double* theta;
   double* phi;
@@ -46,6 +47,7 @@ static ChainView view_of(const rd_chains* c) {
   v.C = c->C;
   v.P = c->P;
   v.seed = c->seed;
+  v.first = c->first_chain;
   for (int j = 0; j < kNParam * kNParam; ++j) v.chol[j] = c->chol[j];
   v.theta = c->theta;
   v.phi = c->phi;
@@ -127,7 +129,7 @@ __global__ void k_chain_propose(DevProblem pb, WorkQueue q, ChainView v, int pus
   if (c >= v.C) return;
   const uint32_t step = (uint32_t)v.ctl[0];
   double u[8], xi[6];
-  chain_uniforms(v.seed, (uint32_t)c, step, u);
+  chain_uniforms(v.seed, v.first + (uint32_t)c, step, u);
   chain_normals(u, xi);
   double th[kNParam];
   for (int j = 0; j < v.P; ++j) {
@@ -161,7 +163,7 @@ __global__ void k_chain_stage1(WorkQueue q, ChainView v) {
   if (c >= v.C) return;
   if (v.prop_status[c] != 0u) return;  // outside the prior's support
   double u[8];
-  chain_uniforms(v.seed, (uint32_t)c, (uint32_t)v.ctl[0], u);
+  chain_uniforms(v.seed, v.first + (uint32_t)c, (uint32_t)v.ctl[0], u);
   const double la1 = (-v.prop_phit[c] + v.prop_lp[c]) - (-v.phit[c] + v.lp[c]);
   if (log(u[6]) < la1) {
     queue_push(q, v.size_idx[c], c);
@@ -177,7 +179,7 @@ __global__ void k_chain_accept_da(ChainView v) {
   if (c >= v.C) return;
   const int slot = v.ctl[1];
   double u[8];
-  chain_uniforms(v.seed, (uint32_t)c, (uint32_t)v.ctl[0], u);
+  chain_uniforms(v.seed, v.first + (uint32_t)c, (uint32_t)v.ctl[0], u);
   const uint32_t st = v.prop_status[c];
   const bool pass1 = (st != RD_P_OUT_OF_SUPPORT && st != kStage1Reject);
   bool acc = false;
@@ -206,7 +208,7 @@ __global__ void k_chain_accept(DevProblem pb, ChainView v) {
   const uint32_t step = (uint32_t)v.ctl[0];
   const int slot = v.ctl[1];
   double u[8];
-  chain_uniforms(v.seed, (uint32_t)c, step, u);
+  chain_uniforms(v.seed, v.first + (uint32_t)c, step, u);
   const uint32_t st = v.prop_status[c];
   bool acc = false;
   if (st == 0u) {
