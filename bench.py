@@ -36,7 +36,12 @@ KERNELS = {"simt": 1, "stacked": 2, "resident": 3}
 # (4096 proposals x 8000 steps at 128^2) of a solve kernel, from one ncu
 # capture of that launch (profiles/); reported only while the SHA-256 of the
 # kernel's sources still matches the one the capture ran on, else null.
-TRAFFIC = {}
+TRAFFIC = {
+    "k_solve2d_tc128<2>": {
+        "sha256": "1a7fe077132e79cf8820421d5f46bedbc22a2595c5d3a61c0f72801f8a9c8c2f",
+        "bytes": 1326336 + 0,  # profiles/k_solve2d_tc128_128sq_traffic.md
+    },
+}
 TRAFFIC_SOURCES = {
     "k_solve2d_tc128<2>": ["rd_solve_tc2.cu", "rd_tc_ptx.cuh", "rd_common.cuh"],
 }
