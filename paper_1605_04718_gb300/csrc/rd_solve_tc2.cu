@@ -21,9 +21,9 @@
 //
 // Pipelining.  The fields u and v run interleaved: while the tensor core
 // works on one field's stage, the other field's converter warps turn the
-// previous result into the next operand.  Stage 3 is also split into two
-// N halves, so its first half starts while the second half of its operand
-// is still being written.
+// previous result into the next operand.  (Splitting a stage into two N = 64
+// halves, to start on half an operand, cost more than it overlapped: an
+// N = 64 MMA takes about 56 cycles against 64 for N = 128.)
 //
 // The diagonal factor L = 1 / (alpha + beta (mu_l + mu_k)) (times 1/64 and
 // the compensation below) is computed where it is applied: the reciprocal by
@@ -75,7 +75,6 @@ constexpr float kScaleW = 0x1p-7f + 0x1p-29f;   // stage 4 (state read): (1/128)
 
 struct Ctrl {
   uint64_t mma_done[2];   // per field: its stage's MMAs completed
-  uint64_t op_half0[2];   // per field: first half of the stage-3 operand written
   uint64_t op_all[2];     // per field: the whole next operand written
   uint64_t rx_ready;      // reaction written (both fields)
   uint64_t st_ready;      // both fields' stage 4 observed
@@ -125,15 +124,14 @@ __device__ __forceinline__ void issue_kmajor(uint8_t* base, uint32_t tmem, int s
   }
 }
 
-// Stage 3 of field f, output columns [64 h, 64 h + 64): B = columns of the
-// MN-major operand tile in 64-column block h, all 128 K rows.
-__device__ __forceinline__ void issue_stage3(uint8_t* base, uint32_t tmem, int f, int h) {
-  constexpr uint32_t idesc = idesc_f16_f32(128, 64, 0, 1);
+// Stage 3 of field f: B = the MN-major operand tile (K rows = lanes of the
+// conversion, two 64-column N blocks 16 KB apart), corrections first.
+__device__ __forceinline__ void issue_stage3(uint8_t* base, uint32_t tmem, int f) {
+  constexpr uint32_t idesc = idesc_f16_f32(128, N, 0, 1);
   const uint32_t a_hi = tmem + kColCtHi, a_lo = tmem + kColCtLo;
-  const uint32_t boff = (uint32_t)h * 16384u;
-  const uint64_t bh = sdesc_sw128(smem_u32(tile(base, f, 0)) + boff, 16384u, 1024u);
-  const uint64_t bl = sdesc_sw128(smem_u32(tile(base, f, 1)) + boff, 16384u, 1024u);
-  const uint32_t d = tmem + kColAcc + (uint32_t)(128 * f + 64 * h);
+  const uint64_t bh = sdesc_sw128(smem_u32(tile(base, f, 0)), 16384u, 1024u);
+  const uint64_t bl = sdesc_sw128(smem_u32(tile(base, f, 1)), 16384u, 1024u);
+  const uint32_t d = tmem + kColAcc + (uint32_t)(128 * f);
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
     const uint64_t off = ((uint32_t)kk * 2048u) >> 4;
@@ -348,11 +346,6 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
             for (int k = 0; k < 32; k += 8) store8(hi_f, lo_f, l, c0 + j + k, a + k, sc);
           }
         }
-        if (stage == 2 && half == 0) {  // stage 3 starts on its first N half
-          fence_proxy_async_smem();
-          tc_fence_before();
-          mbar_arrive(&ctl->op_half0[f]);
-        }
       }
       fence_proxy_async_smem();
       tc_fence_before();
@@ -365,7 +358,7 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
 }
 
 __device__ bool issuer(const DevProblem& pb, Ctrl* ctl, uint8_t* base, uint32_t tmem, int lane,
-                       uint32_t& ph_rx, uint32_t (&ph_h0)[2], uint32_t (&ph_all)[2]) {
+                       uint32_t& ph_rx, uint32_t (&ph_all)[2]) {
   volatile int* abort = &ctl->abort;
   for (int step = 0; step < pb.n_steps; ++step) {
     if (!mbar_wait_bounded(&ctl->rx_ready, ph_rx & 1u, abort)) return false;
@@ -383,19 +376,12 @@ __device__ bool issuer(const DevProblem& pb, Ctrl* ctl, uint8_t* base, uint32_t 
     for (int stage = 2; stage <= 4; ++stage) {
 #pragma unroll
       for (int f = 0; f < 2; ++f) {
-        if (stage == 3) {
-          if (!mbar_wait_bounded(&ctl->op_half0[f], ph_h0[f] & 1u, abort)) return false;
-          ++ph_h0[f];
-          tc_fence_after();
-          if (lane == 0) issue_stage3(base, tmem, f, 0);
-          __syncwarp();
-        }
         if (!mbar_wait_bounded(&ctl->op_all[f], ph_all[f] & 1u, abort)) return false;
         ++ph_all[f];
         tc_fence_after();
         if (lane == 0) {
           if (stage == 3)
-            issue_stage3(base, tmem, f, 1);
+            issue_stage3(base, tmem, f);
           else
             issue_kmajor(base, tmem, stage, f);
           mma_commit(&ctl->mma_done[f]);
@@ -429,7 +415,6 @@ __global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
   if (tid == 0) {
     for (int f = 0; f < 2; ++f) {
       mbar_init(&ctl->mma_done[f], 1);
-      mbar_init(&ctl->op_half0[f], 32 * kConvWarps / 2);
       mbar_init(&ctl->op_all[f], 32 * kConvWarps / 2);
     }
     mbar_init(&ctl->rx_ready, 32 * kConvWarps);
@@ -472,7 +457,7 @@ __global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
   }
   for (int i = tid; i < N; i += kThreads) ctl->mu[i] = S0.mu[i];
   uint32_t ph_done = 0, ph_st = 0, ph_rx = 0;
-  uint32_t ph_h0[2] = {0, 0}, ph_all[2] = {0, 0};
+  uint32_t ph_all[2] = {0, 0};
   for (;;) {
     tc_fence_before();
     __syncthreads();
@@ -514,7 +499,7 @@ __global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
     if (warp < kConvWarps)
       converter<WPF>(pb, S, ctl, base, tmem, warp, lane, ph_done, ph_st, fields, field_stride);
     else
-      issuer(pb, ctl, base, tmem, lane, ph_rx, ph_h0, ph_all);
+      issuer(pb, ctl, base, tmem, lane, ph_rx, ph_all);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
