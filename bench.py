@@ -39,8 +39,8 @@ KERNELS = {"simt": 1, "stacked": 2, "resident": 3}
 # kernel's sources still matches the one the capture ran on, else null.
 TRAFFIC = {
     "k_solve2d_tc128<2>": {
-        "sha256": "1a7fe077132e79cf8820421d5f46bedbc22a2595c5d3a61c0f72801f8a9c8c2f",
-        "bytes": 1326336 + 0,  # profiles/k_solve2d_tc128_128sq_traffic.md
+        "sha256": "9c728bc6d8548e5f5a3e1a5e7c1fde046777a410d7d89d3de93233ab38c9196c",
+        "bytes": 1359616 + 0,  # profiles/k_solve2d_tc128_128sq_traffic.md
     },
 }
 TRAFFIC_SOURCES = {
