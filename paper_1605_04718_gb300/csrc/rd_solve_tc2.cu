@@ -318,34 +318,37 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
       ++ph_done;
       tc_fence_after();
       const float sc = stage == 1 ? kScale1 : stage == 3 ? kScale3 : 1.f;
-#pragma unroll 1
-      for (int half = 0; half < 2; ++half) {
-        const int c0 = 64 * half + CW * rr;
+      // this warp's 64 columns in 4 chunks of 16, the next chunk's TMEM load in
+      // flight while the current one is converted
+      const int cols[4] = {CW * rr, CW * rr + 16, 64 + CW * rr, 64 + CW * rr + 16};
+      float buf[2][16];
+      __syncwarp();
+      tmem_ld16(t_f + (uint32_t)cols[0], buf[0]);
+      tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < CW; j += 32) {
-          float a[32];
-          __syncwarp();
-          tmem_ld32(t_f + (uint32_t)(c0 + j), a);
-          tmem_wait_ld();
-          if (stage == 2) {  // S = D L, L from mu_l + mu_k two columns at a time
-            const uint64_t ml2 = f2_pack(mu_l, mu_l), be2 = f2_pack(beta_f, beta_f);
-            const uint64_t al2 = f2_pack(alpha, alpha), ks2 = f2_pack(kScaleL, kScaleL);
+      for (int q = 0; q < 4; ++q) {
+        float* a = buf[q & 1];
+        if (q < 3) tmem_ld16(t_f + (uint32_t)cols[q + 1], buf[(q + 1) & 1]);
+        const int c0 = cols[q];
+        if (stage == 2) {  // S = D L, L from mu_l + mu_k two columns at a time
+          const uint64_t ml2 = f2_pack(mu_l, mu_l), be2 = f2_pack(beta_f, beta_f);
+          const uint64_t al2 = f2_pack(alpha, alpha), ks2 = f2_pack(kScaleL, kScaleL);
 #pragma unroll
-            for (int k = 0; k < 32; k += 8) {
-              float lam8[8];
+          for (int k = 0; k < 16; k += 8) {
+            float lam8[8];
 #pragma unroll
-              for (int jj = 0; jj < 8; jj += 2) {
-                const float2 mc = *reinterpret_cast<const float2*>(&ctl->mu[c0 + j + k + jj]);
-                const uint64_t x2 = f2_fma(f2_add(ml2, f2_pack(mc.x, mc.y)), be2, al2);
-                f2_unpack(f2_mul(f2_recip(x2), ks2), lam8[jj], lam8[jj + 1]);
-              }
-              store8s(hi_f, lo_f, l, c0 + j + k, a + k, lam8);
+            for (int jj = 0; jj < 8; jj += 2) {
+              const float2 mc = *reinterpret_cast<const float2*>(&ctl->mu[c0 + k + jj]);
+              const uint64_t x2 = f2_fma(f2_add(ml2, f2_pack(mc.x, mc.y)), be2, al2);
+              f2_unpack(f2_mul(f2_recip(x2), ks2), lam8[jj], lam8[jj + 1]);
             }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 32; k += 8) store8(hi_f, lo_f, l, c0 + j + k, a + k, sc);
+            store8s(hi_f, lo_f, l, c0 + k, a + k, lam8);
           }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; k += 8) store8(hi_f, lo_f, l, c0 + k, a + k, sc);
         }
+        if (q < 3) tmem_wait_ld();
       }
       fence_proxy_async_smem();
       tc_fence_before();
