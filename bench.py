@@ -39,8 +39,8 @@ KERNELS = {"simt": 1, "stacked": 2, "resident": 3}
 # kernel's sources still matches the one the capture ran on, else null.
 TRAFFIC = {
     "k_solve2d_tc128<2>": {
-        "sha256": "9c728bc6d8548e5f5a3e1a5e7c1fde046777a410d7d89d3de93233ab38c9196c",
-        "bytes": 1359616 + 0,  # profiles/k_solve2d_tc128_128sq_traffic.md
+        "sha256": "0b71fea7a74859bec6ceb0669f6da8bfb0a9cab6d2f6f2254e34383ac11c6ad3",
+        "bytes": 1243392 + 0,  # profiles/k_solve2d_tc128_128sq_traffic.md
     },
 }
 TRAFFIC_SOURCES = {
