@@ -17,7 +17,10 @@
 //
 // Precision: each FP32 operand x is split into FP16 hi + lo and each product
 // is formed as hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32
-// resolution), giving about 22 significant bits per element.  Power-of-two
+// resolution), giving about 22 significant bits per element.  The small
+// hi*lo and lo*hi products are issued before the hi*hi ones and each stage's
+// output is scaled by 1 + n 2^-29 against the tensor core's round-toward-zero
+// accumulation (tc_rz_comp).  Power-of-two
 // stage scales keep every operand inside the FP16 normal range for field
 // deviations between 0.01 and 100:
 //   R' = 256 r, C' = 8 C  -> P' = 2048 P;   P'' = P' / 128 = 16 P
