@@ -77,6 +77,8 @@ def lib():
                                         ctypes.c_uint32, dp, dp]
         L.orc_chain_randoms_from.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                              ctypes.c_uint32, dp, dp]
+        L.orc_chain_randoms_pt.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                           ctypes.c_uint32, ctypes.c_uint32, dp, dp]
         L.orc_solve1d_thomas.argtypes = [ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, dp, dp]
         L.orc_dct_matrix.argtypes = [ctypes.c_int, dp]
@@ -116,15 +118,16 @@ def philox4x32_10(ctr, key):
     return out
 
 
-def chain_randoms(seed: int, n_chains: int, step: int, first: int = 0):
+def chain_randoms(seed: int, n_chains: int, step: int, first: int = 0, point: int = 0):
     """Normals [C][6] and uniforms [C][2] of every chain at one MCMC step
-    (counters (first + chain, step, 0|1, 0), key = seed; first is the global
-    index of chain 0 when chains are split over processes).  Pinned by moment
-    and distribution tests and by the Philox known-answer values."""
+    (counters (first + chain, step, 0|1, point), key = seed; first is the
+    global index of chain 0 when chains are split over processes, point the
+    index of a point of the multi-proposal step, 0 otherwise).  Pinned by
+    moment and distribution tests and by the Philox known-answer values."""
     normals = np.zeros((n_chains, 6))
     uniforms = np.zeros((n_chains, 2))
-    lib().orc_chain_randoms_from(ctypes.c_uint64(seed), first, n_chains, step,
-                                 _dp(normals), _dp(uniforms))
+    lib().orc_chain_randoms_pt(ctypes.c_uint64(seed), first, n_chains, step, point,
+                               _dp(normals), _dp(uniforms))
     return normals, uniforms
 
 

@@ -16,6 +16,14 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   Phi~ screens each proposal; survivors get the exact Phi and a second test
   min(1, exp(Phi(x) - Phi(x_bar) + Phi~(x_bar) - Phi~(x))), which keeps the
   posterior exact for any surrogate.
+* Algorithm 2 (the multi-proposal parallel Metropolis-Hastings step of
+  Sec. 2.1, Calderhead 2014): N proposals, then the stationary distribution
+  of the (N+1)-state chain A(i, j) = min(1, r(x^i, x^j)) / N (j != i),
+  A(i, i) = 1 - sum_{j != i} A(i, j), r(x, y) = target(y) / target(x), and N
+  draws from it.  Reading: the N proposals are drawn around an auxiliary
+  point z ~ k(x_k, .) (as in the cited method), which makes the proposal of
+  the N+1 points symmetric in them; drawn around x_k itself, as printed, the
+  step would not leave the posterior invariant.
 * Chain workflow of Sec. 2 / 2.1: discard a burn-in fraction, pool chains,
   report means and equal-tailed 95% credible intervals.
 """
@@ -187,6 +195,117 @@ class Chains:
             self.step()
             out[s] = self.theta.T
         return out
+
+
+def pmh_transition_matrix(log_target):
+    """A of Algorithm 2 for the N+1 points with log target values log_target
+    (-inf outside the support): A(i, j) = min(1, r(x^i, x^j)) / N for j != i,
+    r(x^i, x^j) = exp(log_target[j] - log_target[i]), and the diagonal makes
+    each row sum to 1."""
+    lt = np.asarray(log_target, dtype=np.float64)
+    n1 = lt.size
+    N = n1 - 1
+    A = np.zeros((n1, n1))
+    for i in range(n1):
+        for j in range(n1):
+            if j == i:
+                continue
+            if lt[j] == -np.inf:
+                r = 0.0
+            elif lt[i] == -np.inf:
+                r = np.inf
+            else:
+                r = np.exp(lt[j] - lt[i])
+            A[i, j] = min(1.0, r) / N
+        A[i, i] = 1.0 - A[i].sum()
+    return A
+
+
+def stationary(A):
+    """The distribution pi with pi A = pi, sum(pi) = 1 (Algorithm 2 step 3):
+    the linear system A^T pi - pi = 0 with its last equation replaced by the
+    normalisation."""
+    n1 = A.shape[0]
+    M = A.T - np.eye(n1)
+    M[-1, :] = 1.0
+    rhs = np.zeros(n1)
+    rhs[-1] = 1.0
+    return np.linalg.solve(M, rhs)
+
+
+class ParallelChains:
+    """C independent chains advanced by Algorithm 2 with N proposals each;
+    every step yields N samples per chain.  Random numbers of point t of a
+    step (t = 0: the auxiliary point z; t = 1..N: the proposals) come from
+    counters (first + chain, step, 0|1, t); the t-th of the N draws from the
+    stationary distribution uses the uniform u_6 of point t."""
+
+    def __init__(self, model: Model, theta0, seed: int, phi_fn, n_prop: int,
+                 first_chain: int = 0):
+        self.model = model
+        self.theta = np.array(np.atleast_2d(theta0), dtype=np.float64)
+        self.C = self.theta.shape[0]
+        self.N = int(n_prop)
+        self.seed = int(seed)
+        self.first_chain = int(first_chain)
+        self.phi_fn = phi_fn
+        self.step_index = 0
+        self.lp = model.log_prior_eta(self.theta)
+        self.phi, _ = _phi_of(phi_fn, model, self.theta, np.isfinite(self.lp))
+        self.n_prop = self.n_acc = self.n_solves = 0
+
+    def _randoms(self, t):
+        return chain_randoms(self.seed, self.C, self.step_index, self.first_chain, t)
+
+    def _increment(self, xi):
+        m = self.model
+        if m.chol is not None:
+            return xi[:, : m.P] @ np.asarray(m.chol).T
+        return xi[:, : m.P] * np.asarray(m.step)[None, :]
+
+    def step(self):
+        """One step of Algorithm 2; returns the N new samples [N][P][C]."""
+        m, C, N = self.model, self.C, self.N
+        xi0, _ = self._randoms(0)
+        eta_z = m.to_eta(self.theta) + self._increment(xi0)      # auxiliary point
+        props = np.zeros((N, C, m.P))
+        lps = np.zeros((N, C))
+        u_draw = np.zeros((N, C))
+        for t in range(1, N + 1):
+            xi, uu = self._randoms(t)
+            props[t - 1] = m.to_theta(eta_z + self._increment(xi))
+            lps[t - 1] = m.log_prior_eta(props[t - 1])
+            u_draw[t - 1] = uu[:, 0]
+        flat = props.reshape(N * C, m.P)
+        ok = np.isfinite(lps.reshape(-1))
+        phis, _ = _phi_of(self.phi_fn, m, flat, ok)
+        phis = phis.reshape(N, C)
+        self.n_prop += N * C
+        self.n_solves += int(ok.sum())
+        out = np.zeros((N, m.P, C))
+        for c in range(C):
+            pts = np.concatenate([self.theta[c][None, :], props[:, c, :]], 0)
+            phi_c = np.concatenate([[self.phi[c]], phis[:, c]])
+            lp_c = np.concatenate([[self.lp[c]], lps[:, c]])
+            with np.errstate(invalid="ignore"):
+                lt = np.where(np.isfinite(phi_c) & np.isfinite(lp_c), -phi_c + lp_c, -np.inf)
+            pi = stationary(pmh_transition_matrix(lt))
+            cum = np.cumsum(pi)
+            idx = [int(np.searchsorted(cum, u_draw[t, c] * cum[-1], side="right")) for t in range(N)]
+            idx = [min(k, N) for k in idx]
+            for t, k in enumerate(idx):
+                out[t, :, c] = pts[k]
+            self.n_acc += sum(1 for k in idx if k != 0)
+            last = idx[-1]
+            self.theta[c] = pts[last]
+            self.phi[c] = phi_c[last]
+            self.lp[c] = lp_c[last]
+        self.step_index += 1
+        return out
+
+    def run(self, n_steps):
+        """Runs n_steps; returns samples [n_steps * N][P][C]."""
+        return np.concatenate([self.step() for _ in range(n_steps)], 0)
 
 
 def summarize(samples, burn_frac=0.25):

@@ -77,9 +77,10 @@ static double word_to_uniform(uint32_t w) {
 
 /*
  * Random numbers of one chain at one MCMC step.  Two Philox blocks with
- * counters (first + chain, step, 0, 0) and (first + chain, step, 1, 0) --
- * first = the global index of chain 0 when the chains are split over several
- * processes, 0 otherwise -- key = the 64-bit seed
+ * counters (first + chain, step, 0, point) and (first + chain, step, 1,
+ * point) -- first = the global index of chain 0 when the chains are split
+ * over several processes, 0 otherwise; point = 0 for Algorithm 1, the point's
+ * index 0..N under the multi-proposal Algorithm 2 -- key = the 64-bit seed
  * split into (low, high) words, give 8 uniforms u_0..u_7:
  *   u_0..u_5 -> three Box-Muller pairs -> standard normals xi_0..xi_5
  *               (xi_{2j} = sqrt(-2 ln u_{2j}) cos(2 pi u_{2j+1}),
@@ -87,15 +88,15 @@ static double word_to_uniform(uint32_t w) {
  *   u_6       -> the Metropolis (or delayed-acceptance stage-1) uniform;
  *   u_7       -> the delayed-acceptance stage-2 uniform.
  */
-void orc_chain_randoms_from(uint64_t seed, uint32_t first, int n_chains, uint32_t step,
-                            double* normals /* [n_chains][6] */,
-                            double* uniforms /* [n_chains][2] */) {
+void orc_chain_randoms_pt(uint64_t seed, uint32_t first, int n_chains, uint32_t step,
+                          uint32_t point, double* normals /* [n_chains][6] */,
+                          double* uniforms /* [n_chains][2] */) {
   const double two_pi = 6.283185307179586476925286766559;
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   for (int c = 0; c < n_chains; ++c) {
     uint32_t w[8];
-    uint32_t ctr0[4] = {first + (uint32_t)c, step, 0u, 0u};
-    uint32_t ctr1[4] = {first + (uint32_t)c, step, 1u, 0u};
+    uint32_t ctr0[4] = {first + (uint32_t)c, step, 0u, point};
+    uint32_t ctr1[4] = {first + (uint32_t)c, step, 1u, point};
     orc_philox4x32_10(ctr0, key, w);
     orc_philox4x32_10(ctr1, key, w + 4);
     double u[8];
@@ -111,9 +112,14 @@ void orc_chain_randoms_from(uint64_t seed, uint32_t first, int n_chains, uint32_
   }
 }
 
+void orc_chain_randoms_from(uint64_t seed, uint32_t first, int n_chains, uint32_t step,
+                            double* normals, double* uniforms) {
+  orc_chain_randoms_pt(seed, first, n_chains, step, 0u, normals, uniforms);
+}
+
 void orc_chain_randoms(uint64_t seed, int n_chains, uint32_t step, double* normals,
                        double* uniforms) {
-  orc_chain_randoms_from(seed, 0u, n_chains, step, normals, uniforms);
+  orc_chain_randoms_pt(seed, 0u, n_chains, step, 0u, normals, uniforms);
 }
 
 /* ------------------------------------------------------------------------ */
