@@ -92,6 +92,7 @@ enum { RD_PREC_F64 = 0, RD_PREC_F32 = 1 };
 #define RD_MAX_OBS 8
 #define RD_NPARAM 5
 #define RD_NOALLOC_MAX_BATCH 65536
+#define RD_PMH_MAX_PROPOSALS 16 /* N of rd_chains_set_parallel_proposals */
 #define RD_SURROGATE_WIDTH 256
 
 /*
@@ -234,6 +235,24 @@ rd_status rd_chains_set_proposal(rd_chains* c, const double* L);
  * before the first rd_chains_run; it is not part of a checkpoint.  EINVAL if
  * first + n_chains exceeds 2^32. */
 rd_status rd_chains_set_first_chain(rd_chains* c, uint32_t first);
+
+/* Switches the chains to the multi-proposal parallel Metropolis-Hastings step
+ * of Sec. 2.1 (Algorithm 2) with n_prop = N proposals per chain and step
+ * (1..RD_PMH_MAX_PROPOSALS; 0 = back to Algorithm 1).  Per step and chain:
+ * an auxiliary point z = x_k + L xi_0, N proposals z + L xi_t (t = 1..N, the
+ * random numbers of point t at counters (chain, step, 0|1, t)), their
+ * forward solves in the same batched launch as every other chain's, the
+ * stationary distribution of the (N+1)-state chain
+ * A(i, j) = min(1, target(x^j) / target(x^i)) / N (j != i), A(i, i) = 1 - the
+ * row's other entries (solved in FP64), and N draws from it (draw t uses u_6
+ * of point t); the draws are the step's N samples and the last is the new
+ * state.  Proposals drawn around z rather than x_k make the N+1 points'
+ * proposal symmetric, as the method needs to leave the posterior invariant.
+ * Each step then writes N samples to the ring (capacity counts samples), and
+ * rd_chains_read_samples' counters count N proposals per chain-step,
+ * accepted = draws other than x_k.  Allocates the step's buffers; EINVAL with
+ * a surrogate set (delayed acceptance works with Algorithm 1 only). */
+rd_status rd_chains_set_parallel_proposals(rd_chains* c, int n_prop);
 
 /* Advances every chain by n_steps (async; graph-replayed per step).
  * ESTATE if the sample buffer would overflow. */

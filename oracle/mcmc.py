@@ -215,7 +215,8 @@ def pmh_transition_matrix(log_target):
             elif lt[i] == -np.inf:
                 r = np.inf
             else:
-                r = np.exp(lt[j] - lt[i])
+                with np.errstate(over="ignore"):  # exp -> inf, min(1, inf) = 1
+                    r = np.exp(lt[j] - lt[i])
             A[i, j] = min(1.0, r) / N
         A[i, i] = 1.0 - A[i].sum()
     return A

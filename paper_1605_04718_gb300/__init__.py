@@ -29,6 +29,7 @@ RD_PREC_F64, RD_PREC_F32 = 0, 1
 RD_KERNEL_DEFAULT, RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT = range(4)
 RD_MAX_SIZES, RD_MAX_OBS, RD_NPARAM = 4, 8, 5
 RD_NOALLOC_MAX_BATCH = 65536
+RD_PMH_MAX_PROPOSALS = 16
 RD_SURROGATE_WIDTH = 256
 SURROGATE_IN = 16  # padded network inputs
 
@@ -43,6 +44,7 @@ EXPORTS = (
     "rd_surrogate_predict", "rd_surrogate_loss_grad", "rd_surrogate_get_params",
     "rd_surrogate_set_params", "rd_chains_set_surrogate", "rd_chains_set_proposal",
     "rd_set_size_kernel", "rd_get_size_kernel", "rd_autotune", "rd_chains_set_first_chain",
+    "rd_chains_set_parallel_proposals",
 )
 
 
@@ -377,6 +379,12 @@ def rd_chains_set_surrogate(c, s):
 def rd_chains_set_first_chain(c, first):
     """Global index of chain 0 in the random-number counters (sharded runs)."""
     _check(load().rd_chains_set_first_chain(c, ctypes.c_uint32(first)))
+
+
+def rd_chains_set_parallel_proposals(c, n_prop):
+    """Algorithm 2 with n_prop proposals per chain and step (0 = Algorithm 1);
+    each step then yields n_prop samples per chain."""
+    _check(load().rd_chains_set_parallel_proposals(c, n_prop))
 
 
 def rd_chains_set_proposal(c, L):

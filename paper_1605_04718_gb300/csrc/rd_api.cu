@@ -565,6 +565,10 @@ rd_status rd_chains_destroy(rd_chains* c) {
   cudaFree(c->samples);
   cudaFree(c->counters);
   cudaFree(c->ctl);
+  cudaFree(c->pmh_prop);
+  cudaFree(c->pmh_phi);
+  cudaFree(c->pmh_lp);
+  cudaFree(c->pmh_status);
   delete c;
   return RD_OK;
 }
@@ -665,7 +669,8 @@ static rd_status capture_step_graph(rd_chains* c) {
 rd_status rd_chains_run(rd_chains* c, int n_steps) {
   RD_CHECK(c, RD_EINVAL, "chains is NULL");
   RD_CHECK(n_steps >= 0, RD_EINVAL, "n_steps must be >= 0");
-  RD_CHECK(c->ring_host + n_steps <= c->capacity, RD_ESTATE,
+  const long long rows = (long long)n_steps * (c->pmh_n > 0 ? c->pmh_n : 1);
+  RD_CHECK(c->ring_host + rows <= c->capacity, RD_ESTATE,
            "sample buffer full: call rd_chains_read_samples first");
   if (!c->graph_ready || c->graph_generation != c->pb->generation) {
     RD_CUDA(cudaStreamSynchronize(c->pb->stream));
@@ -673,7 +678,7 @@ rd_status rd_chains_run(rd_chains* c, int n_steps) {
     if (r != RD_OK) return r;
   }
   for (int s = 0; s < n_steps; ++s) RD_CUDA(cudaGraphLaunch(c->graph, c->pb->stream));
-  c->ring_host += n_steps;
+  c->ring_host += (int)rows;
   return RD_OK;
 }
 
@@ -698,8 +703,39 @@ rd_status rd_chains_set_first_chain(rd_chains* c, uint32_t first) {
   return RD_OK;
 }
 
+rd_status rd_chains_set_parallel_proposals(rd_chains* c, int n_prop) {
+  RD_CHECK(c, RD_EINVAL, "chains is NULL");
+  RD_CHECK(n_prop >= 0 && n_prop <= RD_PMH_MAX_PROPOSALS, RD_EINVAL,
+           "n_prop must be in 0..RD_PMH_MAX_PROPOSALS");
+  RD_CHECK(n_prop == 0 || c->sur == nullptr, RD_EINVAL,
+           "multi-proposal steps do not combine with a surrogate");
+  RD_CUDA(cudaStreamSynchronize(c->pb->stream));
+  cudaFree(c->pmh_prop);
+  cudaFree(c->pmh_phi);
+  cudaFree(c->pmh_lp);
+  cudaFree(c->pmh_status);
+  c->pmh_prop = nullptr;
+  c->pmh_phi = nullptr;
+  c->pmh_lp = nullptr;
+  c->pmh_status = nullptr;
+  c->pmh_n = 0;
+  c->graph_ready = false;
+  if (n_prop == 0) return RD_OK;
+  const size_t n = (size_t)c->C * n_prop;
+  rd_status r = ensure_capacity(c->pb, (int)n);
+  if (r != RD_OK) return r;
+  RD_CUDA(cudaMalloc(&c->pmh_prop, sizeof(double) * n * c->P));
+  RD_CUDA(cudaMalloc(&c->pmh_phi, sizeof(double) * n));
+  RD_CUDA(cudaMalloc(&c->pmh_lp, sizeof(double) * n));
+  RD_CUDA(cudaMalloc(&c->pmh_status, sizeof(uint32_t) * n));
+  c->pmh_n = n_prop;
+  return RD_OK;
+}
+
 rd_status rd_chains_set_surrogate(rd_chains* c, rd_surrogate* s) {
   RD_CHECK(c, RD_EINVAL, "chains is NULL");
+  RD_CHECK(s == nullptr || c->pmh_n == 0, RD_EINVAL,
+           "delayed acceptance works with single-proposal steps only");
   RD_CUDA(cudaStreamSynchronize(c->pb->stream));
   c->sur = s;
   c->graph_ready = false;  // the step graph differs with and without stage 1

@@ -116,13 +116,15 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0,
 }
 
 // Eight uniforms in (0, 1) of chain `chain` at MCMC step `step`: the words of
-// the Philox blocks at counters (chain, step, 0, 0) and (chain, step, 1, 0)
-// with key (seed low, seed high), each mapped to (w + 1/2) 2^-32.
+// the Philox blocks at counters (chain, step, 0, point) and (chain, step, 1,
+// point) with key (seed low, seed high), each mapped to (w + 1/2) 2^-32.
+// point = 0 except for the points of a multi-proposal step (Algorithm 2).
 __device__ __forceinline__ void chain_uniforms(uint64_t seed, uint32_t chain,
-                                               uint32_t step, double u[8]) {
+                                               uint32_t step, double u[8],
+                                               uint32_t point = 0u) {
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  uint32_t c0[4] = {chain, step, 0u, 0u};
-  uint32_t c1[4] = {chain, step, 1u, 0u};
+  uint32_t c0[4] = {chain, step, 0u, point};
+  uint32_t c1[4] = {chain, step, 1u, point};
   philox4x32_10(c0, k0, k1);
   philox4x32_10(c1, k0, k1);
 #pragma unroll

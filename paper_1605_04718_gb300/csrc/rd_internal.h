@@ -81,6 +81,12 @@ struct rd_chains {
   bool graph_ready = false;
   int graph_generation = -1;
   rd_surrogate* sur = nullptr;  // delayed acceptance when set
+  // multi-proposal steps (Algorithm 2): N proposals per chain and step
+  int pmh_n = 0;
+  double* pmh_prop = nullptr;        // [C][N][P]
+  double* pmh_phi = nullptr;         // [C][N]
+  double* pmh_lp = nullptr;          // [C][N]
+  uint32_t* pmh_status = nullptr;    // [C][N]
 };
 
 namespace rd {

@@ -10,6 +10,9 @@
 // u_0..u_5 -> Box-Muller normals, u_6 -> acceptance uniform (stage-1 uniform
 // under delayed acceptance), u_7 -> stage-2 uniform.
 //
+// Algorithm 2 (multi-proposal parallel Metropolis-Hastings, Sec. 2.1): see
+// k_pmh_propose / k_pmh_select below.
+//
 // Delayed acceptance (Christen & Fox 2005, not in the paper): a surrogate
 // Phi~ screens each proposal; only stage-1 survivors are solved, and the
 // second test min(1, exp(Phi(x) - Phi(x_bar) + Phi~(x_bar) - Phi~(x))) keeps
@@ -40,6 +43,11 @@ struct ChainView {
   double* samples;
   unsigned long long* counters;
   int* ctl;
+  int N;  // proposals per chain and step of Algorithm 2 (0: Algorithm 1)
+  double* pmh_prop;
+  double* pmh_phi;
+  double* pmh_lp;
+  uint32_t* pmh_status;
 };
 
 static ChainView view_of(const rd_chains* c) {
@@ -62,6 +70,11 @@ static ChainView view_of(const rd_chains* c) {
   v.samples = c->samples;
   v.counters = c->counters;
   v.ctl = c->ctl;
+  v.N = c->pmh_n;
+  v.pmh_prop = c->pmh_prop;
+  v.pmh_phi = c->pmh_phi;
+  v.pmh_lp = c->pmh_lp;
+  v.pmh_status = c->pmh_status;
   return v;
 }
 
@@ -229,12 +242,147 @@ __global__ void k_chain_accept(DevProblem pb, ChainView v) {
   v.counters[(size_t)3 * v.C + c] += (st != RD_P_OUT_OF_SUPPORT) ? 1ull : 0ull;
 }
 
-// Ends one MCMC step: advances the step counter and the sample ring, and
-// empties the work lists for the next step.
-__global__ void k_chain_advance(WorkQueue q, int* ctl) {
+// ---------------------------------------------------------------- Algorithm 2
+// Proposal t (1..N) of chain c: z = x + L xi_0 (the auxiliary point, random
+// numbers of point 0), proposal = z + L xi_t (point t), both in step space.
+__global__ void k_pmh_propose(DevProblem pb, WorkQueue q, ChainView v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.C * v.N) return;
+  const int c = i / v.N, t = i - c * v.N + 1;
+  const uint32_t step = (uint32_t)v.ctl[0];
+  double u[8], xi0[6], xi[6];
+  chain_uniforms(v.seed, v.first + (uint32_t)c, step, u, 0u);
+  chain_normals(u, xi0);
+  chain_uniforms(v.seed, v.first + (uint32_t)c, step, u, (uint32_t)t);
+  chain_normals(u, xi);
+  double th[kNParam];
+  for (int j = 0; j < v.P; ++j) {
+    const double x = v.theta[(size_t)c * v.P + j];
+    double inc0 = 0.0, inc = 0.0;
+    for (int k = 0; k <= j; ++k) {
+      inc0 += v.chol[j * kNParam + k] * xi0[k];
+      inc += v.chol[j * kNParam + k] * xi[k];
+    }
+    const bool lg = pb.step_space[j] == RD_STEP_LOG;
+    const double eta = (lg ? log(x) : x) + inc0 + inc;
+    th[j] = lg ? exp(eta) : eta;
+    v.pmh_prop[(size_t)i * v.P + j] = th[j];
+  }
+  const double lp = log_prior_eta(pb, th);
+  v.pmh_lp[i] = lp;
+  if (isfinite(lp)) {
+    v.pmh_status[i] = 0u;
+    queue_push(q, v.size_idx[c], i);
+  } else {
+    v.pmh_status[i] = RD_P_OUT_OF_SUPPORT;
+    v.pmh_phi[i] = (double)INFINITY;
+  }
+}
+
+// The N+1 points' stationary distribution and the N draws of one chain.
+__global__ void k_pmh_select(ChainView v) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.C) return;
+  constexpr int M = RD_PMH_MAX_PROPOSALS + 1;
+  const int N = v.N, n1 = N + 1;
+  const uint32_t step = (uint32_t)v.ctl[0];
+  const int slot = v.ctl[1];
+  // log target of each point (-inf outside the support or for a failed solve)
+  double lt[M];
+  lt[0] = (isfinite(v.phi[c]) && isfinite(v.lp[c])) ? -v.phi[c] + v.lp[c] : -(double)INFINITY;
+  int n_in = 0;
+  for (int t = 1; t <= N; ++t) {
+    const size_t i = (size_t)c * N + t - 1;
+    const bool ok = v.pmh_status[i] == 0u && isfinite(v.pmh_phi[i]);
+    n_in += v.pmh_status[i] != RD_P_OUT_OF_SUPPORT;
+    lt[t] = ok ? -v.pmh_phi[i] + v.pmh_lp[i] : -(double)INFINITY;
+  }
+  // M = A^T - I with the last equation replaced by sum(pi) = 1, where
+  // A(i, j) = min(1, exp(lt_j - lt_i)) / N (j != i), A(i, i) = 1 - row rest
+  double a[M][M + 1];
+  for (int i = 0; i < n1; ++i) {
+    double rest = 0.0;
+    for (int j = 0; j < n1; ++j) {
+      if (j == i) continue;
+      double r;
+      if (lt[j] == -(double)INFINITY)
+        r = 0.0;
+      else if (lt[i] == -(double)INFINITY)
+        r = 1.0;
+      else
+        r = fmin(1.0, exp(lt[j] - lt[i]));
+      a[j][i] = r / N;  // transposed
+      rest += r / N;
+    }
+    a[i][i] = (1.0 - rest) - 1.0;
+  }
+  for (int j = 0; j < n1; ++j) {
+    a[n1 - 1][j] = 1.0;
+    a[j][n1] = 0.0;
+  }
+  a[n1 - 1][n1] = 1.0;
+  // Gaussian elimination with partial pivoting, then back substitution
+  for (int k = 0; k < n1; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n1; ++i)
+      if (fabs(a[i][k]) > fabs(a[piv][k])) piv = i;
+    if (piv != k)
+      for (int j = k; j <= n1; ++j) {
+        const double tmp = a[k][j];
+        a[k][j] = a[piv][j];
+        a[piv][j] = tmp;
+      }
+    for (int i = k + 1; i < n1; ++i) {
+      const double f = a[i][k] / a[k][k];
+      for (int j = k; j <= n1; ++j) a[i][j] -= f * a[k][j];
+    }
+  }
+  double pi[M];
+  for (int i = n1 - 1; i >= 0; --i) {
+    double s = a[i][n1];
+    for (int j = i + 1; j < n1; ++j) s -= a[i][j] * pi[j];
+    pi[i] = s / a[i][i];
+  }
+  double cum[M];
+  double acc_sum = 0.0;
+  for (int i = 0; i < n1; ++i) {
+    acc_sum += pi[i];
+    cum[i] = acc_sum;
+  }
+  // N draws; draw t (1..N) uses u_6 of point t
+  int moved = 0, last = 0;
+  for (int t = 1; t <= N; ++t) {
+    double u[8];
+    chain_uniforms(v.seed, v.first + (uint32_t)c, step, u, (uint32_t)t);
+    const double x = u[6] * cum[n1 - 1];
+    int k = 0;
+    while (k < N && !(x < cum[k])) ++k;
+    moved += k != 0;
+    last = k;
+    for (int j = 0; j < v.P; ++j) {
+      const double th = k == 0 ? v.theta[(size_t)c * v.P + j]
+                               : v.pmh_prop[((size_t)c * N + k - 1) * v.P + j];
+      v.samples[((size_t)(slot + t - 1) * v.P + j) * v.C + c] = th;
+    }
+  }
+  if (last != 0) {
+    const size_t i = (size_t)c * N + last - 1;
+    for (int j = 0; j < v.P; ++j) v.theta[(size_t)c * v.P + j] = v.pmh_prop[i * v.P + j];
+    v.phi[c] = v.pmh_phi[i];
+    v.lp[c] = v.pmh_lp[i];
+  }
+  v.counters[c] += (unsigned long long)N;
+  v.counters[(size_t)v.C + c] += (unsigned long long)n_in;
+  v.counters[(size_t)2 * v.C + c] += (unsigned long long)moved;
+  v.counters[(size_t)3 * v.C + c] += (unsigned long long)n_in;
+}
+
+// Ends one MCMC step: advances the step counter and the sample ring by the
+// step's samples, and empties the work lists for the next step.
+__global__ void k_chain_advance(WorkQueue q, int* ctl, int rows) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctl[0] += 1;
-    ctl[1] += 1;
+    ctl[1] += rows;
   }
   if (threadIdx.x < 2 * kMaxSizes) q.counts[threadIdx.x] = 0;  // counts, pops
 }
@@ -261,6 +409,17 @@ cudaError_t launch_chain_step(rd_chains* c) {
   // the work lists may hold counts from an rd_evaluate_batch call in between
   cudaError_t e = cudaMemsetAsync(q.counts, 0, 2 * kMaxSizes * sizeof(int), p->stream);
   if (e != cudaSuccess) return e;
+  if (c->pmh_n > 0) {  // Algorithm 2
+    const int n = c->C * c->pmh_n;
+    k_pmh_propose<<<(n + 127) / 128, 128, 0, p->stream>>>(p->dev, q, v);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_solve(p, c->pmh_prop, c->pmh_phi, c->pmh_status, nullptr);
+    if (e != cudaSuccess) return e;
+    k_pmh_select<<<blocks, 128, 0, p->stream>>>(v);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_chain_advance<<<1, 32, 0, p->stream>>>(q, c->ctl, c->pmh_n);
+    return cudaGetLastError();
+  }
   const int da = c->sur != nullptr;
   k_chain_propose<<<blocks, 128, 0, p->stream>>>(p->dev, q, v, da ? 0 : 1);
   e = cudaGetLastError();
@@ -278,7 +437,7 @@ cudaError_t launch_chain_step(rd_chains* c) {
   else
     k_chain_accept<<<blocks, 128, 0, p->stream>>>(p->dev, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_chain_advance<<<1, 32, 0, p->stream>>>(q, c->ctl);
+  k_chain_advance<<<1, 32, 0, p->stream>>>(q, c->ctl, 1);
   return cudaGetLastError();
 }
 
