@@ -180,6 +180,15 @@ rd_status rd_evaluate_batch_noalloc(rd_problem* p, int B, const double* theta,
                                     const int* size_idx, double* loglik,
                                     uint32_t* status, void* fields);
 
+/* Restricts the prior to the Turing space of the kinetics (Sec. 3.1.2 Case 2,
+ * eq. (turing)): with enable != 0, log mu0 = -inf unless (a, b, d) -- each
+ * inferred or fixed -- satisfies f_u + g_v < 0, f_u g_v - f_v g_u > 0,
+ * d f_u + g_v > 0 and (d f_u + g_v)^2 - 4 d (f_u g_v - f_v g_u) > 0 at the
+ * homogeneous steady state; inside, the per-parameter priors apply (uniform
+ * boxes give the paper's uniform prior on the Turing space).  Proposals
+ * outside are rejected without a solve.  Default off. */
+rd_status rd_set_turing_prior(rd_problem* p, int enable);
+
 /* Kernel that solves the proposals of grid size `size_idx` (RD_KERNEL_*).
  * Sizes that share a kernel run in one persistent launch; a batch whose sizes
  * use different kernels runs one launch per kernel, in stream order.  EINVAL

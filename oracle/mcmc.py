@@ -49,6 +49,7 @@ class Model:
     step_space: list           # per inferred parameter: "linear" | "log"
     step: np.ndarray           # random-walk standard deviation in step space
     chol: np.ndarray = None    # optional lower-triangular L: eta_bar = eta + L xi
+    turing: bool = False       # also restrict (a, b, d) to the Turing space (Sec. 3.1.2 Case 2)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -99,7 +100,30 @@ class Model:
                 if self.step_space[j] == "log":
                     lpj = lpj + np.log(np.where(t > 0, t, 1.0))
             lp += lpj
+        if self.turing:
+            full = self.full_theta(theta)
+            lp = np.where(in_turing_space(full[:, 0], full[:, 1], full[:, 2]), lp, -np.inf)
         return lp
+
+
+def in_turing_space(a, b, d):
+    """The four inequalities of eq. (turing) for Schnakenberg kinetics at the
+    homogeneous steady state (a + b, b / (a + b)^2): f_u + g_v < 0,
+    f_u g_v - f_v g_u > 0, d f_u + g_v > 0, (d f_u + g_v)^2 - 4 d (f_u g_v -
+    f_v g_u) > 0, with f_u = (b - a)/(b + a), g_v = -(a + b)^2 and
+    f_u g_v - f_v g_u = (a + b)^2.  The uniform prior of Case 2 is uniform on
+    this set (intersected with the box)."""
+    a, b, d = (np.asarray(x, dtype=np.float64) for x in (a, b, d))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = a + b
+        fu = (b - a) / s
+        gv = -s * s
+        det = s * s
+        c1 = fu + gv < 0
+        c2 = det > 0
+        c3 = d * fu + gv > 0
+        c4 = (d * fu + gv) ** 2 - 4 * d * det > 0
+    return c1 & c2 & c3 & c4 & (s > 0)
 
 
 def _phi_of(phi_fn, model, theta, mask):

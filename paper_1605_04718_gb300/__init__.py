@@ -44,7 +44,7 @@ EXPORTS = (
     "rd_surrogate_predict", "rd_surrogate_loss_grad", "rd_surrogate_get_params",
     "rd_surrogate_set_params", "rd_chains_set_surrogate", "rd_chains_set_proposal",
     "rd_set_size_kernel", "rd_get_size_kernel", "rd_autotune", "rd_chains_set_first_chain",
-    "rd_chains_set_parallel_proposals",
+    "rd_chains_set_parallel_proposals", "rd_set_turing_prior",
 )
 
 
@@ -221,6 +221,10 @@ def rd_evaluate_batch_noalloc(p, theta, loglik, status, size_idx=None, fields=No
     serialised by the caller (see include/rdbayes.h)."""
     _check(load().rd_evaluate_batch_noalloc(p, theta.shape[0], _dev_ptr(theta), _dev_ptr(size_idx),
                                             _dev_ptr(loglik), _dev_ptr(status), _dev_ptr(fields)))
+
+
+def rd_set_turing_prior(p, enable=True):
+    _check(load().rd_set_turing_prior(p, 1 if enable else 0))
 
 
 def rd_set_size_kernel(p, size_idx, kernel):

@@ -396,6 +396,13 @@ rd_status rd_set_size_kernel(rd_problem* p, int size_idx, int kernel) {
   return RD_OK;
 }
 
+rd_status rd_set_turing_prior(rd_problem* p, int enable) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  p->dev.turing = enable ? 1 : 0;
+  ++p->generation;  // captured chain steps hold the problem by value
+  return RD_OK;
+}
+
 rd_status rd_get_size_kernel(const rd_problem* p, int size_idx, int* kernel) {
   RD_CHECK(p && kernel, RD_EINVAL, "NULL argument");
   RD_CHECK(size_idx >= 0 && size_idx < p->desc.n_sizes, RD_EINVAL, "size_idx out of range");

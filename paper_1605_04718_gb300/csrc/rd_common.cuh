@@ -49,6 +49,7 @@ struct DevProblem {
   double prior_p0[kNParam];
   double prior_p1[kNParam];
   int step_space[kNParam];
+  int turing;  // prior restricted to the Turing space of (a, b, d)
   DevSize sz[kMaxSizes];
 };
 

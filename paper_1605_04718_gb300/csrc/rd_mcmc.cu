@@ -78,6 +78,21 @@ static ChainView view_of(const rd_chains* c) {
   return v;
 }
 
+// The Turing space of the Schnakenberg kinetics (eq. (turing)) at the
+// homogeneous steady state: f_u + g_v < 0, f_u g_v - f_v g_u > 0,
+// d f_u + g_v > 0, (d f_u + g_v)^2 - 4 d (f_u g_v - f_v g_u) > 0 with
+// f_u = (b - a)/(b + a), g_v = -(a + b)^2, f_u g_v - f_v g_u = (a + b)^2.
+__device__ bool in_turing_space(const DevProblem& pb, const double* th) {
+  double full[kNParam];
+  full_theta(pb, th, full);
+  const double a = full[0], b = full[1], d = full[2];
+  const double s = a + b;
+  if (!(s > 0.0)) return false;
+  const double fu = (b - a) / s, gv = -s * s, det = s * s;
+  const double e = d * fu + gv;
+  return fu + gv < 0.0 && det > 0.0 && e > 0.0 && e * e - 4.0 * d * det > 0.0;
+}
+
 // log mu0(theta) + sum of log |d theta / d eta| over log-stepped parameters;
 // -inf outside the support.  Constants are dropped.
 __device__ double log_prior_eta(const DevProblem& pb, const double* th) {
@@ -99,6 +114,7 @@ __device__ double log_prior_eta(const DevProblem& pb, const double* th) {
     if (pb.step_space[j] == RD_STEP_LOG) lpj = lpj + log(t > 0.0 ? t : 1.0);
     lp += lpj;
   }
+  if (pb.turing && !in_turing_space(pb, th)) lp = -(double)INFINITY;
   return lp;
 }
 

@@ -240,3 +240,39 @@ def test_pmh_reading_auxiliary_point_is_needed():
         ratios[cls] = pooled.var(1) / np.diag(cov)
     assert np.all(np.abs(ratios[mcmc.ParallelChains] - 1.0) < 0.06)
     assert np.all(ratios[Printed] < 0.92)
+
+
+def _unstable_by_dispersion(a, b, d):
+    """Brute force: the homogeneous state is stable without diffusion and some
+    wavenumber k^2 > 0 grows under diffusion, from the eigenvalues of
+    J - k^2 diag(1, d) (J = the Schnakenberg Jacobian at (a + b, b/(a+b)^2))."""
+    s = a + b
+    J = np.array([[(b - a) / s, s * s], [-2 * b / s, -s * s]])
+    if np.max(np.linalg.eigvals(J).real) >= 0:
+        return False
+    ks = np.concatenate([np.linspace(1e-6, 5, 4001), np.geomspace(5, 1e4, 2000)])
+    return any(np.max(np.linalg.eigvals(J - k2 * np.diag([1.0, d])).real) > 0 for k2 in ks)
+
+
+def test_turing_space_matches_the_dispersion_relation():
+    """eq. (turing) against the linear stability of the reaction-diffusion
+    system checked wavenumber by wavenumber."""
+    assert mcmc.in_turing_space(0.1, 0.9, 10.0)
+    assert not mcmc.in_turing_space(0.1, 0.9, 1.0)   # equal diffusion: no patterns
+    rng = np.random.default_rng(11)
+    pts = np.column_stack([rng.uniform(0, 1, 300), rng.uniform(0, 2, 300),
+                           rng.uniform(1, 40, 300)])
+    inside = mcmc.in_turing_space(pts[:, 0], pts[:, 1], pts[:, 2])
+    assert 0.1 < inside.mean() < 0.9
+    for (a, b, d), ins in zip(pts, inside):
+        assert ins == _unstable_by_dispersion(a, b, d), (a, b, d)
+
+
+def test_turing_prior_rejects_outside():
+    m = mcmc.Model(param_map=[0, 1], fixed=np.array([0.1, 0.9, 10.0, 200.0, 0.0]),
+                   prior_kind=["uniform"] * 2, prior_p0=np.array([0.0, 0.0]),
+                   prior_p1=np.array([1.0, 2.0]), step_space=["linear"] * 2,
+                   step=np.array([0.1, 0.1]), turing=True)
+    lp = m.log_prior_eta(np.array([[0.1, 0.9], [0.9, 0.1], [0.5, 1.9]]))
+    assert lp[0] == 0.0 and lp[1] == -np.inf
+    assert (lp[2] == 0.0) == bool(mcmc.in_turing_space(0.5, 1.9, 10.0))
