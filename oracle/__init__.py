@@ -61,7 +61,7 @@ class _Problem(ctypes.Structure):
         ("field_mask", ctypes.c_int), ("y", ctypes.POINTER(ctypes.c_double)),
         ("sigma", ctypes.c_double), ("u0", ctypes.POINTER(ctypes.c_double)),
         ("v0", ctypes.POINTER(ctypes.c_double)), ("w_max", ctypes.c_double),
-        ("solver", ctypes.c_int),
+        ("solver", ctypes.c_int), ("scheme", ctypes.c_int),
     ]
 
 
@@ -180,7 +180,7 @@ class Problem:
 
     def __init__(self, dim, n, tau, n_steps, u0, v0, y=None, obs_steps=None,
                  field_mask=1, sigma=1.0, m_growth=None, w_max=100.0,
-                 solver="dct"):
+                 solver="dct", scheme="imex"):
         self.dim, self.n, self.tau, self.n_steps = dim, n, tau, n_steps
         shape = (n,) if dim == 1 else (n, n)
         self.u0 = np.ascontiguousarray(np.broadcast_to(u0, shape), np.float64)
@@ -196,11 +196,13 @@ class Problem:
         self.m_growth = dim if m_growth is None else m_growth
         self.w_max = w_max
         self.solver = {"dct": 0, "cg": 1}[solver]
+        # 1-D: "imex" (reaction explicit) or "picard" (the paper's semi-implicit step)
+        self.scheme = {"imex": 0, "picard": 1}[scheme]
         self._c = _Problem(
             dim, n, n_steps, tau, self.m_growth, len(self.obs_steps),
             self.obs_steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
             field_mask, _dp(self.y), sigma, _dp(self.u0), _dp(self.v0),
-            w_max, self.solver)
+            w_max, self.solver, self.scheme)
 
     @property
     def shape(self):

@@ -156,6 +156,33 @@ void orc_solve1d_thomas(int n, double alpha, double beta_h, const double* rhs,
   free(dp);
 }
 
+/* 1-D: Thomas algorithm for [diag(alpha_i) - beta_h Lap_h] x = rhs (a
+ * node-dependent alpha, as the linearised reaction terms of the paper's
+ * semi-implicit scheme give). */
+void orc_solve1d_thomas_var(int n, const double* alpha, double beta_h, const double* rhs,
+                            double* x) {
+  double* cp = (double*)malloc(sizeof(double) * (size_t)n);
+  double* dp = (double*)malloc(sizeof(double) * (size_t)n);
+  if (n == 1) {
+    x[0] = rhs[0] / alpha[0];
+    free(cp);
+    free(dp);
+    return;
+  }
+  for (int i = 0; i < n; ++i) {
+    double diag = alpha[i] + ((i == 0 || i == n - 1) ? beta_h : 2.0 * beta_h);
+    double lower = (i > 0) ? -beta_h : 0.0;
+    double upper = (i < n - 1) ? -beta_h : 0.0;
+    double denom = diag - (i > 0 ? lower * cp[i - 1] : 0.0);
+    cp[i] = upper / denom;
+    dp[i] = (rhs[i] - (i > 0 ? lower * dp[i - 1] : 0.0)) / denom;
+  }
+  x[n - 1] = dp[n - 1];
+  for (int i = n - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+  free(cp);
+  free(dp);
+}
+
 /* Orthonormal DCT-II matrix: C[k][i] = c_k cos(pi k (i + 1/2) / N),
  * c_0 = sqrt(1/N), c_k = sqrt(2/N).  Its rows are the eigenvectors of the
  * cell-centred Neumann Laplacian; the eigenvalue of -Lap_h (times h^2) for
@@ -311,6 +338,8 @@ typedef struct {
   const double* v0;
   double w_max;          /* |w| above this at an observation => divergent */
   int solver;            /* 2-D only: 0 = DCT diagonalisation, 1 = CG */
+  int scheme;            /* 1-D only: 0 = IMEX (reaction explicit), 1 = the paper's
+                            semi-implicit scheme (one Picard iterate) */
 } orc_problem;
 
 /*
@@ -321,6 +350,13 @@ typedef struct {
  *   ru = u + tau gamma (a - u + u^2 v),   rv = v + tau gamma (b - u^2 v)
  *   [(1 + tau m r) I - tau / rho_n^2 Lap_h] u^{n+1} = ru
  *   [(1 + tau m r) I - tau d / rho_n^2 Lap_h] v^{n+1} = rv
+ * With scheme = 1 (1-D) the step is the paper's semi-implicit one (Sec. 3.1.1,
+ * Example 1): diffusion, dilution and the linearised reaction implicit, one
+ * Picard iterate (u^n, v^n in the nonlinear coefficients):
+ *   [(1 + tau m r + tau gamma (1 - u^n v^n)) I - tau / rho_n^2 Lap_h] u^{n+1}
+ *       = u^n + tau gamma a
+ *   [(1 + tau m r + tau gamma (u^n)^2) I - tau d / rho_n^2 Lap_h] v^{n+1}
+ *       = v^n + tau gamma b
  * At each observation step the misfit (y - w)^2 / (2 sigma^2) of the observed
  * fields is added to Phi.  Returns the status bits; Phi = +inf if nonzero.
  */
@@ -336,6 +372,8 @@ uint32_t orc_forward(const orc_problem* pb, const double* theta, double* phi_out
   double* v = (double*)malloc(sizeof(double) * npts);
   double* ru = (double*)malloc(sizeof(double) * npts);
   double* rv = (double*)malloc(sizeof(double) * npts);
+  double* t_au = (double*)malloc(sizeof(double) * npts);
+  double* t_av = (double*)malloc(sizeof(double) * npts);
   memcpy(u, pb->u0, sizeof(double) * npts);
   memcpy(v, pb->v0, sizeof(double) * npts);
   double *c = NULL, *mu = NULL, *t = NULL, *s = NULL;
@@ -357,22 +395,33 @@ uint32_t orc_forward(const orc_problem* pb, const double* theta, double* phi_out
     double alpha = 1.0 + tau * pb->m_growth * r;
     double bu = tau * 1.0 / (rho * rho) / (h * h);
     double bv = tau * d / (rho * rho) / (h * h);
-    for (size_t i = 0; i < npts; ++i) {
-      double uu = u[i], vv = v[i];
-      double u2v = uu * uu * vv;
-      ru[i] = uu + tau * g * (a - uu + u2v);
-      rv[i] = vv + tau * g * (b - u2v);
-    }
-    if (pb->dim == 1) {
-      orc_solve1d_thomas(n, alpha, bu, ru, u);
-      orc_solve1d_thomas(n, alpha, bv, rv, v);
-    } else if (pb->solver == 1) {
-      if (orc_solve2d_cg(n, alpha, bu, ru, u, 1e-14, 50 * n * n) < 0 ||
-          orc_solve2d_cg(n, alpha, bv, rv, v, 1e-14, 50 * n * n) < 0)
-        status |= ORC_ST_NOT_CONVERGED;
-    } else {
-      solve2d_dct_ws(n, alpha, bu, c, mu, t, s, ru, u);
-      solve2d_dct_ws(n, alpha, bv, c, mu, t, s, rv, v);
+    if (pb->dim == 1 && pb->scheme == 1) {
+      for (size_t i = 0; i < npts; ++i) {
+        t_au[i] = alpha + tau * g * (1.0 - u[i] * v[i]);
+        t_av[i] = alpha + tau * g * u[i] * u[i];
+        ru[i] = u[i] + tau * g * a;
+        rv[i] = v[i] + tau * g * b;
+      }
+      orc_solve1d_thomas_var(n, t_au, bu, ru, u);
+      orc_solve1d_thomas_var(n, t_av, bv, rv, v);
+    } else {  /* IMEX: reaction explicit */
+      for (size_t i = 0; i < npts; ++i) {
+        double uu = u[i], vv = v[i];
+        double u2v = uu * uu * vv;
+        ru[i] = uu + tau * g * (a - uu + u2v);
+        rv[i] = vv + tau * g * (b - u2v);
+      }
+      if (pb->dim == 1) {
+        orc_solve1d_thomas(n, alpha, bu, ru, u);
+        orc_solve1d_thomas(n, alpha, bv, rv, v);
+      } else if (pb->solver == 1) {
+        if (orc_solve2d_cg(n, alpha, bu, ru, u, 1e-14, 50 * n * n) < 0 ||
+            orc_solve2d_cg(n, alpha, bv, rv, v, 1e-14, 50 * n * n) < 0)
+          status |= ORC_ST_NOT_CONVERGED;
+      } else {
+        solve2d_dct_ws(n, alpha, bu, c, mu, t, s, ru, u);
+        solve2d_dct_ws(n, alpha, bv, c, mu, t, s, rv, v);
+      }
     }
     if (next_obs < pb->n_obs && pb->obs_steps[next_obs] == step + 1) {
       const double* yo = pb->y + (size_t)next_obs * nf_obs * npts;
@@ -402,6 +451,8 @@ uint32_t orc_forward(const orc_problem* pb, const double* theta, double* phi_out
   free(v);
   free(ru);
   free(rv);
+  free(t_au);
+  free(t_av);
   free(c);
   free(mu);
   free(t);

@@ -274,3 +274,65 @@ def test_batch_matches_single():
     for i in range(3):
         p1, s1, _, _ = P.forward(th[i])
         assert s1 == st[i] and (phi[i] == p1 or (np.isinf(p1) and np.isinf(phi[i])))
+
+
+# ---- the paper's semi-implicit scheme (Sec. 3.1.1, Example 1), 1-D --------
+
+def _picard_pair(n, tau, steps, u0, v0, theta):
+    out = {}
+    for scheme in ("imex", "picard"):
+        P = oracle.Problem(1, n, tau, steps, u0, v0, scheme=scheme)
+        out[scheme] = P.forward(theta)[2:4]
+    return out
+
+
+def test_picard_keeps_the_steady_state_fixed():
+    """(a + b, b/(a + b)^2) solves both linearised equations exactly:
+    gamma (1 - u* v*) u* = gamma a and gamma u*^2 v* = gamma b."""
+    a, b = 0.126779, 0.792366
+    us, vs = oracle.steady_state(a, b)
+    P = oracle.Problem(1, 16, 1e-4, 500, np.full(16, us), np.full(16, vs), scheme="picard")
+    _, st, u, v = P.forward([a, b, 10.0, 1000.0, 0.0])
+    assert st == 0
+    assert np.max(np.abs(u - us)) < 1e-13 and np.max(np.abs(v - vs)) < 1e-13
+
+
+def test_picard_equals_imex_without_reaction():
+    """gamma = 0 leaves only the linear diffusion-dilution step, the same in
+    both schemes, bit for bit."""
+    rng = np.random.default_rng(4)
+    u0, v0 = 1 + 0.01 * rng.standard_normal(32), 0.9 + 0.01 * rng.standard_normal(32)
+    out = _picard_pair(32, 1e-3, 200, u0, v0, [0.1, 0.9, 10.0, 0.0, 0.02])
+    assert np.array_equal(out["imex"][0], out["picard"][0])
+    assert np.array_equal(out["imex"][1], out["picard"][1])
+
+
+def test_dilution_of_a_uniform_state():
+    """gamma = 0, uniform state c, growth r: each step divides by
+    1 + tau m r (m = 1 in 1-D), in both schemes."""
+    c, tau, r, steps = 1.3, 1e-3, 0.05, 300
+    for scheme in ("imex", "picard"):
+        P = oracle.Problem(1, 8, tau, steps, np.full(8, c), np.full(8, c), scheme=scheme)
+        _, _, u, _ = P.forward([0.1, 0.9, 10.0, 0.0, r])
+        assert np.allclose(u, c * (1 + tau * r) ** (-steps), rtol=1e-12)
+
+
+def test_picard_and_imex_converge_together_at_first_order():
+    """Both schemes are first order in tau and converge to the same
+    solution: their difference at a fixed time halves with tau, and each
+    one's distance to a fine-tau reference does too."""
+    n, T = 32, 0.02
+    x = (np.arange(n) + 0.5) / n
+    u0 = 1.0 + 0.05 * np.cos(np.pi * x) + 0.02 * np.cos(3 * np.pi * x)
+    v0 = 0.9 - 0.03 * np.cos(2 * np.pi * x)
+    theta = [0.1, 0.9, 10.0, 200.0, 0.0]
+    ref = _picard_pair(n, T / 2048, 2048, u0, v0, theta)["imex"][0]
+    diffs, errs = [], []
+    for k in (64, 128, 256):
+        out = _picard_pair(n, T / k, k, u0, v0, theta)
+        diffs.append(np.max(np.abs(out["picard"][0] - out["imex"][0])))
+        errs.append(np.max(np.abs(out["picard"][0] - ref)))
+    for d0, d1 in zip(diffs, diffs[1:]):
+        assert 0.4 < d1 / d0 < 0.6
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 0.35 < e1 / e0 < 0.65
