@@ -84,6 +84,14 @@ enum {
                                 tensor memory; N = 128 only */
 };
 
+/* Time step of the forward problem (rd_set_scheme). */
+enum {
+  RD_SCHEME_IMEX = 0,   /* reaction explicit, diffusion + dilution implicit */
+  RD_SCHEME_PICARD = 1  /* the paper's semi-implicit step (Sec. 3.1.1, Example 1):
+                           reaction linearised with one Picard iterate and
+                           implicit too; 1-D only */
+};
+
 enum { RD_PRIOR_UNIFORM = 0, RD_PRIOR_LOGNORMAL = 1 };
 enum { RD_STEP_LINEAR = 0, RD_STEP_LOG = 1 };
 enum { RD_PREC_F64 = 0, RD_PREC_F32 = 1 };
@@ -179,6 +187,16 @@ rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
 rd_status rd_evaluate_batch_noalloc(rd_problem* p, int B, const double* theta,
                                     const int* size_idx, double* loglik,
                                     uint32_t* status, void* fields);
+
+/* Time-stepping scheme of the forward solves (RD_SCHEME_*; default IMEX).
+ * RD_SCHEME_PICARD, 1-D problems only: per step
+ *   [(1 + tau m r + tau gamma (1 - u^n v^n)) I - tau / rho_n^2 Lap_h] u^{n+1}
+ *       = u^n + tau gamma a,
+ *   [(1 + tau m r + tau gamma (u^n)^2) I - tau d / rho_n^2 Lap_h] v^{n+1}
+ *       = v^n + tau gamma b,
+ * each a tridiagonal system with a node-dependent diagonal (FP64 Thomas).
+ * EINVAL for an unknown scheme or PICARD on a 2-D problem. */
+rd_status rd_set_scheme(rd_problem* p, int scheme);
 
 /* Restricts the prior to the Turing space of the kinetics (Sec. 3.1.2 Case 2,
  * eq. (turing)): with enable != 0, log mu0 = -inf unless (a, b, d) -- each

@@ -26,6 +26,7 @@ RD_SOLVER_AUTO, RD_SOLVER_THOMAS, RD_SOLVER_DCT_SIMT, RD_SOLVER_DCT_TC = range(4
 RD_PRIOR_UNIFORM, RD_PRIOR_LOGNORMAL = 0, 1
 RD_STEP_LINEAR, RD_STEP_LOG = 0, 1
 RD_PREC_F64, RD_PREC_F32 = 0, 1
+RD_SCHEME_IMEX, RD_SCHEME_PICARD = 0, 1
 RD_KERNEL_DEFAULT, RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT = range(4)
 RD_MAX_SIZES, RD_MAX_OBS, RD_NPARAM = 4, 8, 5
 RD_NOALLOC_MAX_BATCH = 65536
@@ -44,7 +45,7 @@ EXPORTS = (
     "rd_surrogate_predict", "rd_surrogate_loss_grad", "rd_surrogate_get_params",
     "rd_surrogate_set_params", "rd_chains_set_surrogate", "rd_chains_set_proposal",
     "rd_set_size_kernel", "rd_get_size_kernel", "rd_autotune", "rd_chains_set_first_chain",
-    "rd_chains_set_parallel_proposals", "rd_set_turing_prior",
+    "rd_chains_set_parallel_proposals", "rd_set_turing_prior", "rd_set_scheme",
 )
 
 
@@ -221,6 +222,10 @@ def rd_evaluate_batch_noalloc(p, theta, loglik, status, size_idx=None, fields=No
     serialised by the caller (see include/rdbayes.h)."""
     _check(load().rd_evaluate_batch_noalloc(p, theta.shape[0], _dev_ptr(theta), _dev_ptr(size_idx),
                                             _dev_ptr(loglik), _dev_ptr(status), _dev_ptr(fields)))
+
+
+def rd_set_scheme(p, scheme):
+    _check(load().rd_set_scheme(p, scheme))
 
 
 def rd_set_turing_prior(p, enable=True):

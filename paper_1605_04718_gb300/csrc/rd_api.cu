@@ -396,6 +396,16 @@ rd_status rd_set_size_kernel(rd_problem* p, int size_idx, int kernel) {
   return RD_OK;
 }
 
+rd_status rd_set_scheme(rd_problem* p, int scheme) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(scheme == RD_SCHEME_IMEX || scheme == RD_SCHEME_PICARD, RD_EINVAL, "unknown scheme");
+  RD_CHECK(scheme == RD_SCHEME_IMEX || p->desc.dim == 1, RD_EINVAL,
+           "the semi-implicit scheme is built for 1-D problems");
+  p->dev.scheme = scheme;
+  ++p->generation;  // captured chain steps hold the problem by value
+  return RD_OK;
+}
+
 rd_status rd_set_turing_prior(rd_problem* p, int enable) {
   RD_CHECK(p, RD_EINVAL, "problem is NULL");
   p->dev.turing = enable ? 1 : 0;

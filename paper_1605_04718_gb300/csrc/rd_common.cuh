@@ -50,6 +50,7 @@ struct DevProblem {
   double prior_p1[kNParam];
   int step_space[kNParam];
   int turing;  // prior restricted to the Turing space of (a, b, d)
+  int scheme;  // RD_SCHEME_*: 1-D step with the reaction explicit or linearised implicit
   DevSize sz[kMaxSizes];
 };
 

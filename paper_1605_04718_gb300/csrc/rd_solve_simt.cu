@@ -63,6 +63,32 @@ __device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
   thomas_factors<NMAX>(n, alpha, bu, cu, iu);
   thomas_factors<NMAX>(n, alpha, bv, cv, iv);
   for (int step = 0; step < pb.n_steps; ++step) {
+    if (pb.scheme == RD_SCHEME_PICARD) {
+      // the paper's semi-implicit step: the reaction linearised with u^n, v^n
+      // and implicit, so the diagonal varies by node (Thomas, eliminated in
+      // place: cu / cv hold c'_i, ru / rv hold d'_i)
+      const double rho = exp(r * (double)step * tau);
+      const double al = 1.0 + tau * 1.0 * r;  // m = 1 in 1-D
+      const double bu1 = tau / (rho * rho) * h2inv, bv1 = tau * d / (rho * rho) * h2inv;
+      for (int i = 0; i < n; ++i) {
+        const double aui = al + tg * (1.0 - u[i] * v[i]);
+        const double avi = al + tg * u[i] * u[i];
+        const double rU = u[i] + tg * a, rV = v[i] + tg * b;
+        const double edge = (i == 0 || i == n - 1) ? 1.0 : 2.0;
+        const double du = aui + edge * bu1 + (i > 0 ? bu1 * cu[i - 1] : 0.0);
+        const double dv = avi + edge * bv1 + (i > 0 ? bv1 * cv[i - 1] : 0.0);
+        cu[i] = (i < n - 1) ? -bu1 / du : 0.0;
+        cv[i] = (i < n - 1) ? -bv1 / dv : 0.0;
+        ru[i] = (rU + (i > 0 ? bu1 * ru[i - 1] : 0.0)) / du;
+        rv[i] = (rV + (i > 0 ? bv1 * rv[i - 1] : 0.0)) / dv;
+      }
+      u[n - 1] = ru[n - 1];
+      v[n - 1] = rv[n - 1];
+      for (int i = n - 2; i >= 0; --i) {
+        u[i] = ru[i] - cu[i] * u[i + 1];
+        v[i] = rv[i] - cv[i] * v[i + 1];
+      }
+    } else {
     if (grow) {  // rho_n = exp(r t_n): the matrix changes every step
       const double rho = exp(r * (double)step * tau);
       alpha = 1.0 + tau * 1.0 * r;  // m = 1 in 1-D
@@ -88,6 +114,7 @@ __device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
     for (int i = n - 2; i >= 0; --i) {
       u[i] = ru[i] - cu[i] * u[i + 1];
       v[i] = rv[i] - cv[i] * v[i + 1];
+    }
     }
     if (next_obs < S.n_obs && step + 1 == S.obs_steps[next_obs]) {
       const double* yo = S.yd + (size_t)next_obs * nfo * n;
