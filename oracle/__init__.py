@@ -90,6 +90,9 @@ def lib():
                                      ctypes.c_double, dp, dp, ctypes.c_double,
                                      ctypes.c_int]
         L.orc_solve2d_cg.restype = ctypes.c_int
+        L.orc_solve2d_cg_var.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp,
+                                         ctypes.c_double, ctypes.c_int]
+        L.orc_solve2d_cg_var.restype = ctypes.c_int
         L.orc_forward.argtypes = [ctypes.POINTER(_Problem), dp, dp, dp, dp, dp]
         L.orc_forward.restype = ctypes.c_uint32
         L.orc_forward_batch.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int,
@@ -167,6 +170,19 @@ def solve2d_cg(alpha, beta_h, rhs, rtol=1e-14, max_iter=None):
     return x, it
 
 
+def solve2d_cg_var(alpha, beta_h, rhs, rtol=1e-14, max_iter=None):
+    """[diag(alpha) - beta_h Lap_h] x = rhs in 2-D by plain CG (the operator
+    of the paper's semi-implicit step, Sec. 3.1.1).  Pinned against a dense
+    solve."""
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    al = np.ascontiguousarray(np.broadcast_to(alpha, rhs.shape), dtype=np.float64)
+    x = np.zeros_like(rhs)
+    n = rhs.shape[0]
+    it = lib().orc_solve2d_cg_var(n, _dp(al), beta_h, _dp(rhs), _dp(x), rtol,
+                                  max_iter or 50 * n * n)
+    return x, it
+
+
 # --------------------------------------------------------------------------
 # Forward model + log-likelihood (eq. (schnakenberg), (reactions), (logl))
 # --------------------------------------------------------------------------
@@ -196,7 +212,7 @@ class Problem:
         self.m_growth = dim if m_growth is None else m_growth
         self.w_max = w_max
         self.solver = {"dct": 0, "cg": 1}[solver]
-        # 1-D: "imex" (reaction explicit) or "picard" (the paper's semi-implicit step)
+        # "imex" (reaction explicit) or "picard" (the paper's semi-implicit step)
         self.scheme = {"imex": 0, "picard": 1}[scheme]
         self._c = _Problem(
             dim, n, n_steps, tau, self.m_growth, len(self.obs_steps),

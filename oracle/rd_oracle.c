@@ -320,6 +320,66 @@ int orc_solve2d_cg(int n, double alpha, double beta_h, const double* rhs,
   return done ? it : -1;
 }
 
+/* Apply A = diag(alpha_i) - beta_h Lap_h (5-point, Neumann by mirroring):
+ * the operator of the paper's semi-implicit step, whose linearised reaction
+ * terms make the diagonal depend on the node. */
+static void apply_op2d_var(int n, const double* alpha, double beta_h, const double* w,
+                           double* out) {
+  for (int y = 0; y < n; ++y)
+    for (int xx = 0; xx < n; ++xx) {
+      size_t i = (size_t)y * n + xx;
+      double c0 = w[i];
+      double wl = xx > 0 ? w[i - 1] : c0;
+      double wr = xx < n - 1 ? w[i + 1] : c0;
+      double wd = y > 0 ? w[i - n] : c0;
+      double wu = y < n - 1 ? w[i + n] : c0;
+      out[i] = alpha[i] * c0 - beta_h * (wl + wr + wd + wu - 4.0 * c0);
+    }
+}
+
+/* 2-D solve of [diag(alpha_i) - beta_h Lap_h] x = rhs by plain conjugate
+ * gradients (the paper's linear solver), from a zero start, to a relative
+ * residual of rtol.  Returns the iteration count, or -1 if max_iter was
+ * reached. */
+int orc_solve2d_cg_var(int n, const double* alpha, double beta_h, const double* rhs,
+                       double* x, double rtol, int max_iter) {
+  size_t nn = (size_t)n * n;
+  double* r = (double*)malloc(sizeof(double) * nn);
+  double* p = (double*)malloc(sizeof(double) * nn);
+  double* q = (double*)malloc(sizeof(double) * nn);
+  double bnorm2 = 0.0;
+  for (size_t i = 0; i < nn; ++i) {
+    x[i] = 0.0;
+    r[i] = rhs[i];
+    p[i] = rhs[i];
+    bnorm2 += rhs[i] * rhs[i];
+  }
+  double rr = bnorm2;
+  int it = 0;
+  int done = (bnorm2 == 0.0);
+  while (!done && it < max_iter) {
+    apply_op2d_var(n, alpha, beta_h, p, q);
+    double pq = 0.0;
+    for (size_t i = 0; i < nn; ++i) pq += p[i] * q[i];
+    double step = rr / pq;
+    double rr_new = 0.0;
+    for (size_t i = 0; i < nn; ++i) {
+      x[i] += step * p[i];
+      r[i] -= step * q[i];
+      rr_new += r[i] * r[i];
+    }
+    ++it;
+    if (rr_new <= rtol * rtol * bnorm2) done = 1;
+    double beta_cg = rr_new / rr;
+    rr = rr_new;
+    for (size_t i = 0; i < nn; ++i) p[i] = r[i] + beta_cg * p[i];
+  }
+  free(r);
+  free(p);
+  free(q);
+  return done ? it : -1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Forward model and log-likelihood                                          */
 /* ------------------------------------------------------------------------ */
@@ -338,7 +398,7 @@ typedef struct {
   const double* v0;
   double w_max;          /* |w| above this at an observation => divergent */
   int solver;            /* 2-D only: 0 = DCT diagonalisation, 1 = CG */
-  int scheme;            /* 1-D only: 0 = IMEX (reaction explicit), 1 = the paper's
+  int scheme;            /* 0 = IMEX (reaction explicit), 1 = the paper's
                             semi-implicit scheme (one Picard iterate) */
 } orc_problem;
 
@@ -350,9 +410,10 @@ typedef struct {
  *   ru = u + tau gamma (a - u + u^2 v),   rv = v + tau gamma (b - u^2 v)
  *   [(1 + tau m r) I - tau / rho_n^2 Lap_h] u^{n+1} = ru
  *   [(1 + tau m r) I - tau d / rho_n^2 Lap_h] v^{n+1} = rv
- * With scheme = 1 (1-D) the step is the paper's semi-implicit one (Sec. 3.1.1,
+ * With scheme = 1 the step is the paper's semi-implicit one (Sec. 3.1.1,
  * Example 1): diffusion, dilution and the linearised reaction implicit, one
- * Picard iterate (u^n, v^n in the nonlinear coefficients):
+ * Picard iterate (u^n, v^n in the nonlinear coefficients), each system
+ * solved by the Thomas algorithm (1-D) or plain CG to 1e-14 (2-D):
  *   [(1 + tau m r + tau gamma (1 - u^n v^n)) I - tau / rho_n^2 Lap_h] u^{n+1}
  *       = u^n + tau gamma a
  *   [(1 + tau m r + tau gamma (u^n)^2) I - tau d / rho_n^2 Lap_h] v^{n+1}
@@ -395,15 +456,20 @@ uint32_t orc_forward(const orc_problem* pb, const double* theta, double* phi_out
     double alpha = 1.0 + tau * pb->m_growth * r;
     double bu = tau * 1.0 / (rho * rho) / (h * h);
     double bv = tau * d / (rho * rho) / (h * h);
-    if (pb->dim == 1 && pb->scheme == 1) {
+    if (pb->scheme == 1) {
       for (size_t i = 0; i < npts; ++i) {
         t_au[i] = alpha + tau * g * (1.0 - u[i] * v[i]);
         t_av[i] = alpha + tau * g * u[i] * u[i];
         ru[i] = u[i] + tau * g * a;
         rv[i] = v[i] + tau * g * b;
       }
-      orc_solve1d_thomas_var(n, t_au, bu, ru, u);
-      orc_solve1d_thomas_var(n, t_av, bv, rv, v);
+      if (pb->dim == 1) {
+        orc_solve1d_thomas_var(n, t_au, bu, ru, u);
+        orc_solve1d_thomas_var(n, t_av, bv, rv, v);
+      } else if (orc_solve2d_cg_var(n, t_au, bu, ru, u, 1e-14, 50 * n * n) < 0 ||
+                 orc_solve2d_cg_var(n, t_av, bv, rv, v, 1e-14, 50 * n * n) < 0) {
+        status |= ORC_ST_NOT_CONVERGED;
+      }
     } else {  /* IMEX: reaction explicit */
       for (size_t i = 0; i < npts; ++i) {
         double uu = u[i], vv = v[i];

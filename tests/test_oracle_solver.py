@@ -336,3 +336,76 @@ def test_picard_and_imex_converge_together_at_first_order():
         assert 0.4 < d1 / d0 < 0.6
     for e0, e1 in zip(errs, errs[1:]):
         assert 0.35 < e1 / e0 < 0.65
+
+
+# ---- the paper's semi-implicit scheme in 2-D (Sec. 3.1.1) ------------------
+
+def _neumann_1d(n):
+    """Unscaled 3-point Neumann Laplacian (ghost values mirror the boundary)."""
+    L = -2.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    L[0, 0] = L[-1, -1] = -1.0
+    return L
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_2d_variable_diagonal_cg_matches_dense_solve(n):
+    """[diag(alpha) - beta Lap_h] x = rhs, with alpha varying by node, against
+    the dense 2-D operator built as a Kronecker sum (brute force)."""
+    rng = np.random.default_rng(n)
+    alpha = 1.0 + 0.3 * rng.random((n, n))
+    rhs = rng.standard_normal((n, n))
+    beta = 3.7
+    L1 = _neumann_1d(n)
+    A = np.diag(alpha.reshape(-1)) - beta * (np.kron(np.eye(n), L1) + np.kron(L1, np.eye(n)))
+    ref = np.linalg.solve(A, rhs.reshape(-1)).reshape(n, n)
+    x, it = oracle.solve2d_cg_var(alpha, beta, rhs)
+    assert it > 0
+    assert np.max(np.abs(x - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_picard_2d_keeps_the_steady_state_fixed():
+    """As in 1-D: the homogeneous steady state solves both linearised 2-D
+    equations exactly (to the CG tolerance)."""
+    a, b = 0.126779, 0.792366
+    us, vs = oracle.steady_state(a, b)
+    n = 8
+    P = oracle.Problem(2, n, 1e-4, 50, np.full((n, n), us), np.full((n, n), vs),
+                       scheme="picard")
+    _, st, u, v = P.forward([a, b, 10.0, 1000.0, 0.0])
+    assert st == 0
+    assert np.max(np.abs(u - us)) < 1e-12 and np.max(np.abs(v - vs)) < 1e-12
+
+
+def test_picard_2d_equals_imex_without_reaction():
+    """gamma = 0: both schemes take the same linear diffusion-dilution step
+    (eigenbasis solve against CG, equal to the CG tolerance)."""
+    n = 8
+    rng = np.random.default_rng(5)
+    u0 = 1 + 0.01 * rng.standard_normal((n, n))
+    v0 = 0.9 + 0.01 * rng.standard_normal((n, n))
+    out = {}
+    for scheme in ("imex", "picard"):
+        P = oracle.Problem(2, n, 1e-3, 40, u0, v0, scheme=scheme)
+        out[scheme] = P.forward([0.1, 0.9, 10.0, 0.0, 0.02])[2:4]
+    for f in range(2):
+        assert np.max(np.abs(out["imex"][f] - out["picard"][f])) < 1e-12
+
+
+def test_picard_2d_and_imex_converge_together_at_first_order():
+    """Both 2-D schemes are first order in tau with the same limit: their
+    difference at a fixed time halves with tau."""
+    n, T = 8, 0.01
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    u0 = 1.0 + 0.05 * np.cos(np.pi * X) * np.cos(np.pi * Y) + 0.02 * np.cos(3 * np.pi * X)
+    v0 = 0.9 - 0.03 * np.cos(2 * np.pi * Y)
+    theta = [0.1, 0.9, 10.0, 200.0, 0.0]
+    diffs = []
+    for k in (32, 64, 128):
+        out = {}
+        for scheme in ("imex", "picard"):
+            P = oracle.Problem(2, n, T / k, k, u0, v0, scheme=scheme)
+            out[scheme] = P.forward(theta)[2]
+        diffs.append(np.max(np.abs(out["picard"] - out["imex"])))
+    for d0, d1 in zip(diffs, diffs[1:]):
+        assert 0.4 < d1 / d0 < 0.6, diffs
