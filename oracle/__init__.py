@@ -62,7 +62,13 @@ class _Problem(ctypes.Structure):
         ("sigma", ctypes.c_double), ("u0", ctypes.POINTER(ctypes.c_double)),
         ("v0", ctypes.POINTER(ctypes.c_double)), ("w_max", ctypes.c_double),
         ("solver", ctypes.c_int), ("scheme", ctypes.c_int),
+        ("growth_kind", ctypes.c_int), ("rho_T", ctypes.c_double),
+        ("logistic_K", ctypes.c_double),
     ]
+
+
+NPHYS = 8  # (a, b, d, gamma, r, p1, p2, p3)
+GROWTH = {"exp": 0, "poly4": 1, "logistic": 2}
 
 
 def lib():
@@ -93,6 +99,8 @@ def lib():
         L.orc_solve2d_cg_var.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp,
                                          ctypes.c_double, ctypes.c_int]
         L.orc_solve2d_cg_var.restype = ctypes.c_int
+        L.orc_growth.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, dp, dp]
         L.orc_forward.argtypes = [ctypes.POINTER(_Problem), dp, dp, dp, dp, dp]
         L.orc_forward.restype = ctypes.c_uint32
         L.orc_forward_batch.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int,
@@ -196,7 +204,7 @@ class Problem:
 
     def __init__(self, dim, n, tau, n_steps, u0, v0, y=None, obs_steps=None,
                  field_mask=1, sigma=1.0, m_growth=None, w_max=100.0,
-                 solver="dct", scheme="imex"):
+                 solver="dct", scheme="imex", growth="exp", rho_T=1.0, logistic_K=1.0):
         self.dim, self.n, self.tau, self.n_steps = dim, n, tau, n_steps
         shape = (n,) if dim == 1 else (n, n)
         self.u0 = np.ascontiguousarray(np.broadcast_to(u0, shape), np.float64)
@@ -214,21 +222,24 @@ class Problem:
         self.solver = {"dct": 0, "cg": 1}[solver]
         # "imex" (reaction explicit) or "picard" (the paper's semi-implicit step)
         self.scheme = {"imex": 0, "picard": 1}[scheme]
+        # law of rho(t): "exp" (r = theta[4]), "poly4" (Example 1's polynomial,
+        # theta[5:8] and rho_T) or "logistic" (rate theta[4], capacity logistic_K)
+        self.growth = GROWTH[growth]
         self._c = _Problem(
             dim, n, n_steps, tau, self.m_growth, len(self.obs_steps),
             self.obs_steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
             field_mask, _dp(self.y), sigma, _dp(self.u0), _dp(self.v0),
-            w_max, self.solver, self.scheme)
+            w_max, self.solver, self.scheme, self.growth, rho_T, logistic_K)
 
     @property
     def shape(self):
         return (self.n,) if self.dim == 1 else (self.n, self.n)
 
     def forward(self, theta, want_obs=False):
-        """Solve at theta = (a, b, d, gamma, r); returns (phi, status, u, v)
-        and, with want_obs, also the observed fields at the observation steps
-        ([n_obs][observed fields][...])."""
-        th = np.zeros(5)
+        """Solve at theta = (a, b, d, gamma, r[, p1, p2, p3]); returns (phi,
+        status, u, v) and, with want_obs, also the observed fields at the
+        observation steps ([n_obs][observed fields][...])."""
+        th = np.zeros(NPHYS)
         th[: len(theta)] = theta
         u = np.zeros(self.shape)
         v = np.zeros(self.shape)
@@ -242,10 +253,10 @@ class Problem:
         return phi.value, int(st), u, v
 
     def forward_batch(self, thetas, n_threads=None, want_fields=False):
-        """Solves for thetas [B][5] on host threads; returns (phi, status[, fields])."""
+        """Solves for thetas [B][5 or 8] on host threads; returns (phi, status[, fields])."""
         th = np.ascontiguousarray(thetas, dtype=np.float64)
-        if th.shape[1] < 5:
-            th = np.concatenate([th, np.zeros((th.shape[0], 5 - th.shape[1]))], 1)
+        if th.shape[1] < NPHYS:
+            th = np.concatenate([th, np.zeros((th.shape[0], NPHYS - th.shape[1]))], 1)
         B = th.shape[0]
         phi = np.zeros(B)
         status = np.zeros(B, dtype=np.uint32)
@@ -258,6 +269,29 @@ class Problem:
         if want_fields:
             return phi, status, fields
         return phi, status
+
+
+def growth(kind, theta, t, T, rho_T=1.0, logistic_K=1.0):
+    """(rho(t), rho'(t) / rho(t)) of the growth law `kind` (see Problem)."""
+    th = np.zeros(NPHYS)
+    th[: len(theta)] = theta
+    rho, q = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    lib().orc_growth(GROWTH[kind], _dp(th), rho_T, logistic_K, T, t, ctypes.byref(rho),
+                     ctypes.byref(q))
+    return rho.value, q.value
+
+
+def poly4_positive(p, rho_T, n_check=1000):
+    """Whether Example 1's polynomial rho(s) = 1 + p1 s + p2 s^2 + p3 s^3 +
+    p4 s^4 (p4 = rho_T - 1 - p1 - p2 - p3) is positive at s = k / n_check,
+    k = 0..n_check: the support of the growth prior (rho > 0 on [0, T]).
+    p: [..., 3]."""
+    p = np.asarray(p, dtype=np.float64)
+    p1, p2, p3 = p[..., 0:1], p[..., 1:2], p[..., 2:3]
+    p4 = rho_T - 1.0 - p1 - p2 - p3
+    sv = np.arange(n_check + 1) / n_check
+    rho = 1.0 + sv * (p1 + sv * (p2 + sv * (p3 + sv * p4)))
+    return np.all(rho > 0.0, axis=-1)
 
 
 def steady_state(a, b):

@@ -50,6 +50,7 @@ class Model:
     step: np.ndarray           # random-walk standard deviation in step space
     chol: np.ndarray = None    # optional lower-triangular L: eta_bar = eta + L xi
     turing: bool = False       # also restrict (a, b, d) to the Turing space (Sec. 3.1.2 Case 2)
+    poly_rho_T: float = None   # Example 1: also require the polynomial rho(t) > 0 on [0, T]
     extra: dict = field(default_factory=dict)
 
     @property
@@ -57,9 +58,11 @@ class Model:
         return len(self.param_map)
 
     def full_theta(self, theta):
-        """[C][P] inferred values -> [C][5] (a, b, d, gamma, r)."""
+        """[C][P] inferred values -> [C][8] (a, b, d, gamma, r, p1, p2, p3)."""
         theta = np.atleast_2d(theta)
-        out = np.tile(np.asarray(self.fixed, dtype=np.float64), (theta.shape[0], 1))
+        fixed = np.zeros(8)
+        fixed[: len(self.fixed)] = self.fixed
+        out = np.tile(fixed, (theta.shape[0], 1))
         for j, idx in enumerate(self.param_map):
             out[:, idx] = theta[:, j]
         return out
@@ -103,6 +106,10 @@ class Model:
         if self.turing:
             full = self.full_theta(theta)
             lp = np.where(in_turing_space(full[:, 0], full[:, 1], full[:, 2]), lp, -np.inf)
+        if self.poly_rho_T is not None:
+            from . import poly4_positive
+            full = self.full_theta(theta)
+            lp = np.where(poly4_positive(full[:, 5:8], self.poly_rho_T), lp, -np.inf)
         return lp
 
 

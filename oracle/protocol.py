@@ -13,6 +13,7 @@ data with the FP64 oracle; nothing here runs on the GPU path.
   the threshold too.
 * Measurement: the stationary field plus Gaussian noise whose standard
   deviation is a fraction (5 % or 10 %) of the field's range.
+* Example 1's initial state, eq. (ic_gturing).
 """
 from __future__ import annotations
 
@@ -34,6 +35,16 @@ def paper_initial_state(dim, n, a, b):
         pert = 0.0016 * np.cos(2 * np.pi * (X + Y)) + 0.01 * sum(
             np.cos(2 * np.pi * j * X) for j in range(1, 9))
     return us + pert, vs + pert
+
+
+def example1_initial_state(n):
+    """Initial state of eq. (ic_gturing) (Example 1) on the cell-centred grid
+    x_i = (i + 1/2) / n of the unit interval: the homogeneous steady state
+    (1, 0.9) of a = 0.1, b = 0.9 plus 0.005 sum_{k=1..9} sin(k pi x) in both
+    fields; returns (u0, v0)."""
+    x = (np.arange(n) + 0.5) / n
+    pert = 0.005 * sum(np.sin(k * np.pi * x) for k in range(1, 10))
+    return 1.0 + pert, 0.9 + pert
 
 
 def _l2(w, h, dim):

@@ -37,6 +37,7 @@
 #define ORC_ST_OUT_OF_SUPPORT 1u
 #define ORC_ST_NONFINITE 2u
 #define ORC_ST_NOT_CONVERGED 4u
+#define ORC_NPHYS 8 /* (a, b, d, gamma, r, p1, p2, p3) */
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al. 2011): 10 rounds of the 4x32 S-box            */
@@ -400,26 +401,68 @@ typedef struct {
   int solver;            /* 2-D only: 0 = DCT diagonalisation, 1 = CG */
   int scheme;            /* 0 = IMEX (reaction explicit), 1 = the paper's
                             semi-implicit scheme (one Picard iterate) */
+  int growth_kind;       /* ORC_GROWTH_*: the law of rho(t) (orc_growth) */
+  double rho_T;          /* polynomial law: the known final size rho(T) */
+  double logistic_K;     /* logistic law: the carrying capacity */
 } orc_problem;
+
+/* Domain growth laws rho(t) of eq. (schnakenberg), rho(0) = 1:
+ *  ORC_GROWTH_EXP:      rho = exp(r t), r = theta[4] (r = 0: fixed domain);
+ *  ORC_GROWTH_POLY4:    the finite-dimensional approximation of Example 1
+ *    (Sec. 3.1.1): a degree-4 polynomial in s = t / T with the coefficients of
+ *    order 0 and 4 fixed by rho(0) = 1 and rho(T) = rho_T, so three degrees
+ *    of freedom p1, p2, p3 = theta[5..7]:
+ *      rho = 1 + p1 s + p2 s^2 + p3 s^3 + p4 s^4,  p4 = rho_T - 1 - p1 - p2 - p3;
+ *  ORC_GROWTH_LOGISTIC: eq. (grates)' logistic law with rate lambda = theta[4]
+ *    and carrying capacity K, rho = e^{lambda t} / (1 + (e^{lambda t} - 1) / K),
+ *    the solution of rho' = lambda rho (1 - rho / K). */
+#define ORC_GROWTH_EXP 0
+#define ORC_GROWTH_POLY4 1
+#define ORC_GROWTH_LOGISTIC 2
+
+/* rho(t) and rho'(t) / rho(t) of the law `kind` (T = final time). */
+void orc_growth(int kind, const double* theta, double rho_T, double K, double T, double t,
+                double* rho, double* rdot_over_rho) {
+  if (kind == ORC_GROWTH_POLY4) {
+    const double p1 = theta[5], p2 = theta[6], p3 = theta[7];
+    const double p4 = rho_T - 1.0 - p1 - p2 - p3;
+    const double sv = t / T;
+    const double r = 1.0 + sv * (p1 + sv * (p2 + sv * (p3 + sv * p4)));
+    const double drds = p1 + sv * (2.0 * p2 + sv * (3.0 * p3 + sv * 4.0 * p4));
+    *rho = r;
+    *rdot_over_rho = drds / T / r;
+  } else if (kind == ORC_GROWTH_LOGISTIC) {
+    const double lam = theta[4];
+    const double e = exp(lam * t);
+    const double r = e / (1.0 + (e - 1.0) / K);
+    *rho = r;
+    *rdot_over_rho = lam * (1.0 - r / K);
+  } else {
+    *rho = exp(theta[4] * t);
+    *rdot_over_rho = theta[4];
+  }
+}
 
 /*
  * One forward solve G(p) and its log-likelihood Phi(p; y).
- * theta = (a, b, d, gamma, r): kinetics of eq. (reactions), diffusion ratio d,
- * scale gamma, and growth rate r of rho(t) = exp(r t) (r = 0: fixed domain).
- * Step n -> n+1 (t_n = n tau, rho_n = exp(r t_n), rho'/rho = r):
+ * theta = (a, b, d, gamma, r, p1, p2, p3): kinetics of eq. (reactions),
+ * diffusion ratio d, scale gamma, and the growth law's parameters (orc_growth;
+ * r = 0 with the exponential law: fixed domain).
+ * Step n -> n+1 (t_n = n tau, rho_n = rho(t_n), q_n = rho'(t_n) / rho(t_n)):
  *   ru = u + tau gamma (a - u + u^2 v),   rv = v + tau gamma (b - u^2 v)
- *   [(1 + tau m r) I - tau / rho_n^2 Lap_h] u^{n+1} = ru
- *   [(1 + tau m r) I - tau d / rho_n^2 Lap_h] v^{n+1} = rv
+ *   [(1 + tau m q_n) I - tau / rho_n^2 Lap_h] u^{n+1} = ru
+ *   [(1 + tau m q_n) I - tau d / rho_n^2 Lap_h] v^{n+1} = rv
  * With scheme = 1 the step is the paper's semi-implicit one (Sec. 3.1.1,
  * Example 1): diffusion, dilution and the linearised reaction implicit, one
  * Picard iterate (u^n, v^n in the nonlinear coefficients), each system
  * solved by the Thomas algorithm (1-D) or plain CG to 1e-14 (2-D):
- *   [(1 + tau m r + tau gamma (1 - u^n v^n)) I - tau / rho_n^2 Lap_h] u^{n+1}
+ *   [(1 + tau m q_n + tau gamma (1 - u^n v^n)) I - tau / rho_n^2 Lap_h] u^{n+1}
  *       = u^n + tau gamma a
- *   [(1 + tau m r + tau gamma (u^n)^2) I - tau d / rho_n^2 Lap_h] v^{n+1}
+ *   [(1 + tau m q_n + tau gamma (u^n)^2) I - tau d / rho_n^2 Lap_h] v^{n+1}
  *       = v^n + tau gamma b
  * At each observation step the misfit (y - w)^2 / (2 sigma^2) of the observed
- * fields is added to Phi.  Returns the status bits; Phi = +inf if nonzero.
+ * fields is added to Phi.  A growth law that reaches rho <= 0 flags the solve
+ * non-finite.  Returns the status bits; Phi = +inf if nonzero.
  */
 uint32_t orc_forward(const orc_problem* pb, const double* theta, double* phi_out,
                      double* u_out, double* v_out, double* obs_out) {
@@ -450,10 +493,20 @@ uint32_t orc_forward(const orc_problem* pb, const double* theta, double* phi_out
   uint32_t status = 0;
   int next_obs = 0;
   const int nf_obs = ((pb->field_mask & 1) ? 1 : 0) + ((pb->field_mask & 2) ? 1 : 0);
+  const double T_final = (double)pb->n_steps * tau;
   for (int step = 0; step < pb->n_steps; ++step) {
     double t_n = (double)step * tau;
     double rho = exp(r * t_n);
     double alpha = 1.0 + tau * pb->m_growth * r;
+    if (pb->growth_kind != ORC_GROWTH_EXP) {
+      double q;
+      orc_growth(pb->growth_kind, theta, pb->rho_T, pb->logistic_K, T_final, t_n, &rho, &q);
+      if (!(rho > 0.0)) {
+        status |= ORC_ST_NONFINITE;
+        break;
+      }
+      alpha = 1.0 + tau * pb->m_growth * q;
+    }
     double bu = tau * 1.0 / (rho * rho) / (h * h);
     double bv = tau * d / (rho * rho) / (h * h);
     if (pb->scheme == 1) {
@@ -541,12 +594,13 @@ static void* batch_worker(void* arg) {
   for (int i = j->begin; i < j->end; ++i) {
     double* uo = j->fields ? j->fields + (size_t)i * 2 * npts : NULL;
     double* vo = j->fields ? uo + npts : NULL;
-    j->status[i] = orc_forward(j->pb, j->theta + (size_t)i * 5, &j->phi[i], uo, vo, NULL);
+    j->status[i] = orc_forward(j->pb, j->theta + (size_t)i * ORC_NPHYS, &j->phi[i], uo, vo,
+                               NULL);
   }
   return NULL;
 }
 
-/* Forward solves for B parameter vectors ([B][5]) on n_threads host threads,
+/* Forward solves for B parameter vectors ([B][ORC_NPHYS]) on n_threads host threads,
  * one proposal per thread at a time. */
 void orc_forward_batch(const orc_problem* pb, int B, const double* theta,
                        double* phi, uint32_t* status, double* fields,

@@ -33,6 +33,21 @@ DATASETS = {
                            theta=(0.1, 0.9, 10.0, 200.0, 0.01),
                            obs_frac=(0.2, 0.4, 0.6, 0.8, 1.0), field_mask=1, sigma=0.02,
                            ic_amp=0.01, ic_seed=40, obs_seed=41, dtype="f32"),
+    # Example 1 (Sec. 3.1.1): 1-D growing interval, fixed kinetics, the paper's
+    # semi-implicit scheme, h = 1e-2, tau = 1e-4, T = 600; data from the
+    # exponential law exp(0.001 t) or the logistic law (rate 0.01, capacity
+    # exp(0.6)); the initial state of eq. (ic_gturing); u and v observed at T
+    # with noise of 5 % of the range of u
+    "rd1d_e1_exp": dict(dim=1, n=100, tau=1e-4, n_steps=6_000_000,
+                        theta=(0.1, 0.9, 10.0, 1000.0, 0.001), growth="exp",
+                        logistic_K=1.0, scheme="picard", ic="example1",
+                        obs_frac=(1.0,), field_mask=3, noise_frac=0.05, obs_seed=51,
+                        dtype="f64"),
+    "rd1d_e1_log": dict(dim=1, n=100, tau=1e-4, n_steps=6_000_000,
+                        theta=(0.1, 0.9, 10.0, 1000.0, 0.01), growth="logistic",
+                        logistic_K=float(np.exp(0.6)), scheme="picard", ic="example1",
+                        obs_frac=(1.0,), field_mask=3, noise_frac=0.05, obs_seed=52,
+                        dtype="f64"),
 }
 
 
