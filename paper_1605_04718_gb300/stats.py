@@ -64,6 +64,21 @@ def split_rhat(samples):
     return float(np.sqrt(var_plus / W)) if W > 0 else float("nan")
 
 
+def mcse_quantile(samples, prob):
+    """Monte Carlo standard error of the prob-quantile of samples
+    [steps][chains], after Vehtari et al. (2021): the effective size S of the
+    indicator x <= q gives the spread sqrt(prob (1 - prob) / S) of the
+    quantile's level, and half the width of the pooled-sample interval
+    between the levels prob -+ that spread is the standard error (their Beta
+    interval in its normal limit)."""
+    x = np.asarray(samples, dtype=np.float64)
+    q = np.quantile(x, prob)
+    s_eff = ess((x <= q).astype(np.float64))
+    d = np.sqrt(prob * (1.0 - prob) / max(s_eff, 1.0))
+    lo, hi = max(prob - d, 0.0), min(prob + d, 1.0)
+    return float(0.5 * (np.quantile(x, hi) - np.quantile(x, lo)))
+
+
 def summarize(samples, burn_frac=0.25, names=None):
     """samples [steps][P][chains] -> per-parameter mean, sd, equal-tailed 95%
     interval, ESS, MCSE of the mean and split-R-hat after burn-in."""
@@ -79,5 +94,6 @@ def summarize(samples, burn_frac=0.25, names=None):
             "mean": float(x.mean()), "sd": sd,
             "q025": float(np.quantile(x, 0.025)), "q975": float(np.quantile(x, 0.975)),
             "ess": e, "mcse": sd / np.sqrt(e), "rhat": split_rhat(x),
+            "mcse_q025": mcse_quantile(x, 0.025), "mcse_q975": mcse_quantile(x, 0.975),
         })
     return out

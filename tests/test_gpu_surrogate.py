@@ -219,3 +219,63 @@ def test_delayed_acceptance_chains_match_oracle_posterior():
         rd.rd_chains_destroy(h)
     rd.rd_surrogate_destroy(s)
     rd.rd_problem_destroy(p)
+
+
+def test_trained_surrogate_cuts_exact_solves_per_effective_sample():
+    """What the learned part gains: a surrogate trained on the GPU by the
+    library's own kernels, on (theta, Phi) pairs the batched solver produced,
+    screens delayed-acceptance proposals so that the exact solves spent per
+    effective sample fall well below plain Metropolis' (one solve per
+    proposal), while both samplers reach the same posterior: means and 95%
+    interval ends within 3 combined Monte Carlo standard errors."""
+    from paper_1605_04718_gb300 import stats
+    ds = H.small_dataset(32, 100, seed=13, sigma=0.05)
+    p = H.gpu_problem([ds], solver=rd.RD_SOLVER_DCT_TC)
+    C = 128
+    theta0 = rd_synth.chain_starts([0.1, 0.9, 10.0, 200.0], C, seed=31)
+    step = np.array([0.02, 0.01, 0.05, 0.05])
+    # pilot: burn in with plain chains, then a proposal covariance from them
+    c = rd.rd_chains_create(p, theta0, 5, step, capacity=400)
+    rd.rd_chains_run(c, 400)
+    pilot, _ = rd.rd_chains_read_samples(c, 400, 4, C)
+    start, _ = rd.rd_chains_get_state(c, 4, C)
+    rd.rd_chains_destroy(c)
+    lt = np.log(pilot[200:]).transpose(1, 0, 2).reshape(4, -1)
+    mu, cov = lt.mean(1), np.cov(lt)
+    prop = np.linalg.cholesky(2.38 ** 2 / 4 * cov)
+    # training pairs from the batched exact solver, 2.5 posterior sd around it
+    n = 4096
+    th_tr = np.exp(mu[None, :] + 2.5 * np.random.default_rng(3).standard_normal((n, 4))
+                   @ np.linalg.cholesky(cov).T)
+    th_d = torch.tensor(th_tr, dtype=torch.float64, device=DEV)
+    phi_d = torch.zeros(n, dtype=torch.float64, device=DEV)
+    st_d = torch.zeros(n, dtype=torch.int32, device=DEV)
+    rd.rd_evaluate_batch(p, th_d, phi_d, st_d)
+    rd.rd_sync(p)
+    s = rd.rd_surrogate_create(p, seed=6)
+    rep = rd.rd_surrogate_train(s, th_d, phi_d, epochs=80, batch=512, lr=1e-3,
+                                holdout_frac=0.1, seed=2)
+    assert np.all(np.isfinite(rep))
+    S = 1200
+    out = {}
+    for mode in ("plain", "da"):
+        c = rd.rd_chains_create(p, start, 4242, step, capacity=S)
+        rd.rd_chains_set_proposal(c, prop)
+        if mode == "da":
+            rd.rd_chains_set_surrogate(c, s)
+        rd.rd_chains_run(c, S)
+        smp, cnt = rd.rd_chains_read_samples(c, S, 4, C)
+        rd.rd_chains_destroy(c)
+        summ = stats.summarize(smp, burn_frac=0.25)
+        ess = min(x["ess"] for x in summ)
+        out[mode] = (summ, cnt[3] * 0.75 / ess, cnt)
+    assert out["plain"][2][3] == out["plain"][2][0]  # plain: one solve per proposal
+    assert out["da"][2][3] < 0.6 * out["da"][2][0]    # DA: only stage-1 survivors
+    # exact solves per effective sample
+    assert out["da"][1] < 0.7 * out["plain"][1], (out["da"][1], out["plain"][1])
+    for a, b in zip(out["da"][0], out["plain"][0]):
+        assert abs(a["mean"] - b["mean"]) < 3 * np.hypot(a["mcse"], b["mcse"]), (a, b)
+        assert abs(a["q025"] - b["q025"]) < 3 * np.hypot(a["mcse_q025"], b["mcse_q025"]), (a, b)
+        assert abs(a["q975"] - b["q975"]) < 3 * np.hypot(a["mcse_q975"], b["mcse_q975"]), (a, b)
+    rd.rd_surrogate_destroy(s)
+    rd.rd_problem_destroy(p)

@@ -42,3 +42,31 @@ def test_summarize_matches_pooled_quantiles():
     assert out[0]["q025"] == pytest.approx(-1.96, abs=0.1)
     assert out[1]["sd"] == pytest.approx(3.0, rel=0.05)
     assert out[0]["ess"] == pytest.approx(800 * 8, rel=0.15)
+
+
+@pytest.mark.parametrize("prob", [0.025, 0.5, 0.975])
+def test_quantile_mcse_of_independent_normals(prob):
+    """For n independent N(0, 1) draws the quantile's standard error is
+    sqrt(p (1 - p) / n) / phi(z_p) (the asymptotic variance of a sample
+    quantile); the estimator must reproduce it, and the spread of the
+    quantile over repeated samples must match it."""
+    from statistics import NormalDist
+    n, m = 4000, 8
+    nd = NormalDist()
+    z = nd.inv_cdf(prob)
+    expect = np.sqrt(prob * (1 - prob) / (n * m)) / nd.pdf(z)
+    rng = np.random.default_rng(int(1000 * prob))
+    got = [stats.mcse_quantile(rng.standard_normal((n, m)), prob) for _ in range(3)]
+    assert np.mean(got) == pytest.approx(expect, rel=0.15)
+    reps = [np.quantile(rng.standard_normal((n, m)), prob) for _ in range(200)]
+    assert np.std(reps) == pytest.approx(expect, rel=0.2)
+
+
+def test_quantile_mcse_grows_with_autocorrelation():
+    """AR(1) chains with coefficient 0.9 carry (1 - 0.9)/(1 + 0.9) of the
+    information of independent draws: the quantile's standard error grows
+    by about sqrt(19)."""
+    x = _ar1(0.9, 8000, 8, 3) * np.sqrt(1 - 0.81)  # unit marginal variance
+    y = np.random.default_rng(4).standard_normal((8000, 8))
+    r = stats.mcse_quantile(x, 0.5) / stats.mcse_quantile(y, 0.5)
+    assert r == pytest.approx(np.sqrt(19.0), rel=0.3)
