@@ -17,8 +17,9 @@
  * Conventions for every call:
  *  - Returns an rd_status; never aborts.  rd_last_error() gives a message
  *    for the calling thread.
- *  - Parameter vectors are in natural units, in the order (a, b, d, gamma, r)
- *    mapped through rd_problem_desc.param_map.
+ *  - Parameter vectors are in natural units, in the order of the inferred
+ *    model parameters (a, b, d, gamma, r, p1, p2, p3) that
+ *    rd_problem_desc.param_map lists.
  *  - "device" pointers are CUDA device addresses on the problem's device;
  *    "host" pointers are ordinary host memory.  The caller owns every pointer
  *    it passes; the library copies or consumes inputs in stream order and
@@ -59,7 +60,9 @@ enum {
   RD_P_OK = 0,
   RD_P_OUT_OF_SUPPORT = 1, /* prior density zero: rejected without a solve */
   RD_P_NONFINITE = 2,      /* non-finite or |w| > w_max at an observation */
-  RD_P_NOT_CONVERGED = 4   /* iterative solve hit its iteration cap */
+  RD_P_NOT_CONVERGED = 4,  /* iterative solve hit its iteration cap */
+  RD_P_NOT_SOLVED = 8      /* queued, but no solve kernel finished it (a bounded
+                              wait gave up: the call reports RD_ETIMEOUT) */
 };
 
 /* Implicit-diffusion solver of the IMEX step. */
@@ -80,8 +83,12 @@ enum {
   RD_KERNEL_SIMT = 1,        /* FP32 CUDA-core GEMMs, one proposal per CTA */
   RD_KERNEL_TC_STACKED = 2,  /* split-FP16 tcgen05, DCT matrix in shared memory,
                                 floor(128/N) proposals stacked per MMA tile */
-  RD_KERNEL_TC_RESIDENT = 3  /* split-FP16 tcgen05, DCT matrices resident in
+  RD_KERNEL_TC_RESIDENT = 3, /* split-FP16 tcgen05, DCT matrices resident in
                                 tensor memory; N = 128 only */
+  RD_KERNEL_CG = 4           /* each implicit system by plain conjugate gradients
+                                (the paper's linear solver, Sec. 3.1.1) from the
+                                previous step, FP32 on CUDA cores, vectors in
+                                shared memory; every grid of the problem N <= 96 */
 };
 
 /* Time step of the forward problem (rd_set_scheme). */
@@ -89,16 +96,28 @@ enum {
   RD_SCHEME_IMEX = 0,   /* reaction explicit, diffusion + dilution implicit */
   RD_SCHEME_PICARD = 1  /* the paper's semi-implicit step (Sec. 3.1.1, Example 1):
                            reaction linearised with one Picard iterate and
-                           implicit too; 1-D only */
+                           implicit too; 1-D, or 2-D with every grid N <= 80 */
 };
 
 enum { RD_PRIOR_UNIFORM = 0, RD_PRIOR_LOGNORMAL = 1 };
+/* Domain growth law rho(t) of eq. (schnakenberg) (rd_problem_desc.growth). */
+enum {
+  RD_GROWTH_NONE = 0,  /* fixed domain, rho = 1 */
+  RD_GROWTH_EXP = 1,   /* rho = exp(r t), m = dim (r = model parameter 4) */
+  RD_GROWTH_POLY4 = 2  /* Example 1 (Sec. 3.1.1): rho(s), s = t / T, T = n_steps tau,
+                          = 1 + p1 s + p2 s^2 + p3 s^3 + p4 s^4 with
+                          p4 = rho_T - 1 - p1 - p2 - p3, so rho(0) = 1 and
+                          rho(T) = rho_T; p1..p3 = model parameters 5..7;
+                          1-D only.  The prior also requires rho > 0 at
+                          s = k / 1000, k = 0..1000 */
+};
 enum { RD_STEP_LINEAR = 0, RD_STEP_LOG = 1 };
 enum { RD_PREC_F64 = 0, RD_PREC_F32 = 1 };
 
 #define RD_MAX_SIZES 4
 #define RD_MAX_OBS 8
-#define RD_NPARAM 5
+#define RD_NPARAM 5  /* inferred parameters at most */
+#define RD_NPHYS 8   /* model parameters (a, b, d, gamma, r, p1, p2, p3) */
 #define RD_NOALLOC_MAX_BATCH 65536
 #define RD_PMH_MAX_PROPOSALS 16 /* N of rd_chains_set_parallel_proposals */
 #define RD_SURROGATE_WIDTH 256
@@ -118,15 +137,20 @@ typedef struct {
   int n_steps;                /* steps to the final time T = n_steps * tau */
   int precision;              /* RD_PREC_F64 (1-D) or RD_PREC_F32 (2-D fields) */
   int solver;                 /* RD_SOLVER_* */
-  int growth;                 /* 0: rho = 1 (r ignored); 1: rho = exp(r t), m = dim */
+  int growth;                 /* RD_GROWTH_*: 0 fixed domain (r ignored), 1 exponential,
+                                 2 Example 1's polynomial */
   int n_params;               /* number of inferred parameters P, 1..5 */
-  int param_map[RD_NPARAM];   /* index in (a, b, d, gamma, r) of inferred parameter j */
-  double fixed[RD_NPARAM];    /* values of the parameters that are not inferred */
+  int param_map[RD_NPARAM];   /* index in (a, b, d, gamma, r, p1, p2, p3) of inferred
+                                 parameter j (5..7 only with RD_GROWTH_POLY4) */
+  double fixed[RD_NPARAM];    /* values of the model parameters 0..4 that are not
+                                 inferred */
   int prior_kind[RD_NPARAM];  /* per inferred parameter: RD_PRIOR_* */
   double prior_p0[RD_NPARAM]; /* uniform: lower bound; log-normal: median */
   double prior_p1[RD_NPARAM]; /* uniform: upper bound; log-normal: sigma of log */
   int step_space[RD_NPARAM];  /* per inferred parameter: RD_STEP_* */
   double w_max;               /* divergence bound (<= 0: default 100) */
+  double fixed_poly[3];       /* RD_GROWTH_POLY4: values of p1..p3 not inferred */
+  double rho_T;               /* RD_GROWTH_POLY4: the known final size rho(T) */
 } rd_problem_desc;
 
 /* Creates a problem on the current CUDA device and stream `cuda_stream`.
@@ -164,7 +188,8 @@ rd_status rd_evaluate_batch(rd_problem* p, int B, const double* theta,
                             uint32_t* status, void* fields);
 
 /* As rd_evaluate_batch with HOST theta/size_idx/loglik/status: copies in,
- * solves, copies out, and returns when the results are in host memory. */
+ * solves, copies out, and returns when the results are in host memory;
+ * RD_ETIMEOUT as rd_sync. */
 rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
                                  const int* size_idx, double* loglik,
                                  uint32_t* status);
@@ -179,9 +204,10 @@ rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
  * call allocates nothing: the solve kernels' work lists live in one fixed
  * device array of the library (about 1 MiB, held on every GPU that loads the
  * library until the process exits), so B may be at most RD_NOALLOC_MAX_BATCH
- * (EINVAL beyond).  The problem's device must be current.  The first call on
- * a device also looks up that array's device address (no allocation); make
- * that first call before any stream capture.  All calls share the array and
+ * (EINVAL beyond).  The problem's device must be current.  rd_problem_create
+ * looks up that array's device address once per device (which loads the array
+ * onto the device), so the first call on a device is allocation-free too and
+ * needs no set-up of its own.  All calls share the array and
  * each clears its counters before use, so calls whose GPU work overlaps (for
  * example on two streams at once) race and must be serialised by the caller. */
 rd_status rd_evaluate_batch_noalloc(rd_problem* p, int B, const double* theta,
@@ -189,14 +215,43 @@ rd_status rd_evaluate_batch_noalloc(rd_problem* p, int B, const double* theta,
                                     uint32_t* status, void* fields);
 
 /* Time-stepping scheme of the forward solves (RD_SCHEME_*; default IMEX).
- * RD_SCHEME_PICARD, 1-D problems only: per step
+ * RD_SCHEME_PICARD: per step
  *   [(1 + tau m r + tau gamma (1 - u^n v^n)) I - tau / rho_n^2 Lap_h] u^{n+1}
  *       = u^n + tau gamma a,
  *   [(1 + tau m r + tau gamma (u^n)^2) I - tau d / rho_n^2 Lap_h] v^{n+1}
  *       = v^n + tau gamma b,
- * each a tridiagonal system with a node-dependent diagonal (FP64 Thomas).
- * EINVAL for an unknown scheme or PICARD on a 2-D problem. */
+ * each a system with a node-dependent diagonal: in 1-D tridiagonal (FP64
+ * Thomas); in 2-D (FP32 fields) solved by conjugate gradients preconditioned
+ * with the eigenbasis solve of the operator with the mean diagonal, to a
+ * relative residual of 1e-6 (a proposal whose solve reaches the iteration
+ * cap gets RD_P_NOT_CONVERGED), all sizes in one CUDA-core launch whatever
+ * kernel each size has.  EINVAL for an unknown scheme or PICARD on a 2-D
+ * problem with a grid above 80. */
 rd_status rd_set_scheme(rd_problem* p, int scheme);
+
+/* Steady-state forward map (the measurement protocol of Sec. 3.1.2: the data
+ * are the stationary pattern).  With threshold > 0 every forward solve runs
+ * until the first step T at which the L2 norm of the discrete time
+ * derivative, (h^dim sum over both fields and all nodes of
+ * ((w^T - w^{T-1}) / tau)^2)^(1/2), is below threshold (1e-5 in the paper),
+ * at most n_steps steps; the misfit is taken against the problem's single
+ * observation (each size must have exactly one observation time, whose step
+ * index is then ignored) at T, and the final fields are w(T).  With
+ * confirm != 0 the solve continues to 2T and requires the same norm of
+ * w(2T) - w(T) to be below threshold (the paper's check that the state is
+ * stationary).  A solve that reaches neither gets RD_P_NOT_CONVERGED.
+ * Fixed domains only (EINVAL with growth); 2-D problems need every grid
+ * N <= 96 and run on the CUDA-core eigenbasis kernel (the tensor-core
+ * kernels hold no copy of the previous step), 1-D on the FP64 Thomas kernel.
+ * threshold = 0 turns the mode off.  Takes effect at the next launch. */
+rd_status rd_set_steady_state(rd_problem* p, double threshold, int confirm);
+
+/* rd_evaluate_batch in steady-state mode that also writes T per proposal
+ * (device int [B]; 0 where no steady state was reached).  ESTATE when the
+ * mode is off. */
+rd_status rd_evaluate_batch_steady(rd_problem* p, int B, const double* theta,
+                                   const int* size_idx, double* loglik,
+                                   uint32_t* status, void* fields, int* steps);
 
 /* Restricts the prior to the Turing space of the kinetics (Sec. 3.1.2 Case 2,
  * eq. (turing)): with enable != 0, log mu0 = -inf unless (a, b, d) -- each
@@ -217,16 +272,27 @@ rd_status rd_set_size_kernel(rd_problem* p, int size_idx, int kernel);
 /* The kernel size `size_idx` runs with, RD_KERNEL_DEFAULT resolved. */
 rd_status rd_get_size_kernel(const rd_problem* p, int size_idx, int* kernel);
 
+/* Schedule of grid size `size_idx`'s persistent launch: CTAs per SM
+ * (0..32; 0 = as many as fit, the default).  Sizes sharing a kernel launch
+ * run with the largest value any of them sets, capped at what fits.  Takes
+ * effect at the next launch. */
+rd_status rd_set_size_schedule(rd_problem* p, int size_idx, int ctas_per_sm);
+/* The CTAs per SM that size's launch uses (default and cap resolved). */
+rd_status rd_get_size_schedule(const rd_problem* p, int size_idx, int* ctas_per_sm);
+
 /* Timed search of the solve kernel of every grid size of a 2-D problem:
  * for each size s, solves the B proposals theta (host, [B][n_params], the
  * same batch for every candidate) as size s with each kernel that supports
  * it, one warm-up and n_trials timed launches (CUDA events on the problem's
  * stream), probe_steps IMEX steps per solve (0 = the problem's n_steps), and
- * sets the kernel with the lowest median time (rd_set_size_kernel).  Sizes
+ * sets the kernel and schedule with the lowest median time
+ * (rd_set_size_kernel, rd_set_size_schedule): every kernel is timed at 1, 2,
+ * 4, ... persistent CTAs per SM up to what fits on an SM.  Sizes
  * of a problem run one persistent launch per kernel kind, so the choice per
  * size stays within one batched evaluation.  times_out (host, may be NULL):
- * [n_sizes][3] seconds per proposal for RD_KERNEL_SIMT, TC_STACKED and
- * TC_RESIDENT, NaN where a kernel does not apply.  Allocates scratch for the
+ * [n_sizes][4] seconds per proposal for RD_KERNEL_SIMT, TC_STACKED,
+ * TC_RESIDENT and CG at each one's best schedule, NaN where a kernel does
+ * not apply.  Allocates scratch for the
  * batch; synchronises the stream.  EINVAL for a 1-D problem; on a failed
  * launch the previous choices are kept. */
 rd_status rd_autotune(rd_problem* p, int B, const double* theta, int n_trials, int probe_steps,
@@ -366,8 +432,29 @@ rd_status rd_surrogate_set_params(rd_surrogate* s, const float* buf, size_t n,
  * u_7).  The surrogate must outlive its use by the chains. */
 rd_status rd_chains_set_surrogate(rd_chains* c, rd_surrogate* s);
 
-/* Blocks until all work enqueued on the problem's stream has finished. */
+/* Blocks until all work enqueued on the problem's stream has finished, then
+ * returns RD_ETIMEOUT (and clears the flag) if a solve kernel's bounded wait
+ * gave up since the last check: its unsolved proposals keep status
+ * RD_P_NOT_SOLVED and Phi = +inf. */
 rd_status rd_sync(rd_problem* p);
+
+/* Limit of every bounded wait inside the tensor-core solve kernels (default
+ * 4 s; (0, 60] seconds).  A healthy wait lasts microseconds; a wait that runs
+ * out makes the kernel's CTA stop popping work, drain the MMAs it issued,
+ * free its tensor memory and raise the problem's error flag, which rd_sync and
+ * rd_evaluate_batch_host report as RD_ETIMEOUT.  The context stays usable.
+ * Takes effect at the next launch (captured chain steps are re-captured). */
+rd_status rd_set_wait_limit(rd_problem* p, double seconds);
+
+/* Test aid for the failure path above (not part of the method): with
+ * step >= 0, the MMA-issuing warp of every tensor-core solve CTA, after
+ * issuing stage 1 of IMEX step `step` of its first proposal, waits on a
+ * barrier that nothing completes instead of going on.  That wait, and then
+ * every other wait of the CTA, runs out after the wait limit, so the launch
+ * ends in bounded time with RD_ETIMEOUT and every proposal of the batch left
+ * RD_P_NOT_SOLVED.  step = -1 (the default) turns it off.  CUDA-core kernels
+ * have no waits and ignore it. */
+rd_status rd_debug_stall_at_step(rd_problem* p, int step);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* rd_last_error(void);

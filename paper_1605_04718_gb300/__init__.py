@@ -21,14 +21,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librdbayes.so")
 
 RD_OK, RD_EINVAL, RD_ENOMEM, RD_ECUDA, RD_ESTATE, RD_ETIMEOUT = range(6)
-RD_P_OK, RD_P_OUT_OF_SUPPORT, RD_P_NONFINITE, RD_P_NOT_CONVERGED = 0, 1, 2, 4
+RD_P_OK, RD_P_OUT_OF_SUPPORT, RD_P_NONFINITE, RD_P_NOT_CONVERGED, RD_P_NOT_SOLVED = 0, 1, 2, 4, 8
 RD_SOLVER_AUTO, RD_SOLVER_THOMAS, RD_SOLVER_DCT_SIMT, RD_SOLVER_DCT_TC = range(4)
 RD_PRIOR_UNIFORM, RD_PRIOR_LOGNORMAL = 0, 1
 RD_STEP_LINEAR, RD_STEP_LOG = 0, 1
 RD_PREC_F64, RD_PREC_F32 = 0, 1
 RD_SCHEME_IMEX, RD_SCHEME_PICARD = 0, 1
-RD_KERNEL_DEFAULT, RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT = range(4)
-RD_MAX_SIZES, RD_MAX_OBS, RD_NPARAM = 4, 8, 5
+RD_KERNEL_DEFAULT, RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT, RD_KERNEL_CG = range(5)
+RD_MAX_SIZES, RD_MAX_OBS, RD_NPARAM, RD_NPHYS = 4, 8, 5, 8
+RD_GROWTH_NONE, RD_GROWTH_EXP, RD_GROWTH_POLY4 = 0, 1, 2
 RD_NOALLOC_MAX_BATCH = 65536
 RD_PMH_MAX_PROPOSALS = 16
 RD_SURROGATE_WIDTH = 256
@@ -46,6 +47,8 @@ EXPORTS = (
     "rd_surrogate_set_params", "rd_chains_set_surrogate", "rd_chains_set_proposal",
     "rd_set_size_kernel", "rd_get_size_kernel", "rd_autotune", "rd_chains_set_first_chain",
     "rd_chains_set_parallel_proposals", "rd_set_turing_prior", "rd_set_scheme",
+    "rd_set_wait_limit", "rd_debug_stall_at_step", "rd_set_steady_state",
+    "rd_evaluate_batch_steady", "rd_set_size_schedule", "rd_get_size_schedule",
 )
 
 
@@ -67,6 +70,7 @@ class rd_problem_desc(ctypes.Structure):
         ("prior_p0", ctypes.c_double * RD_NPARAM),
         ("prior_p1", ctypes.c_double * RD_NPARAM),
         ("step_space", ctypes.c_int * RD_NPARAM), ("w_max", ctypes.c_double),
+        ("fixed_poly", ctypes.c_double * 3), ("rho_T", ctypes.c_double),
     ]
 
 
@@ -120,6 +124,9 @@ def load():
     L.rd_surrogate_set_params.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.rd_chains_set_surrogate.argtypes = [vp, vp]
     L.rd_chains_set_proposal.argtypes = [vp, vp]
+    L.rd_set_wait_limit.argtypes = [vp, d]
+    L.rd_set_steady_state.argtypes = [vp, d, i]
+    L.rd_evaluate_batch_steady.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
     L.rd_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "rd_last_error":
@@ -156,7 +163,7 @@ def _stream_handle(stream):
 
 def make_desc(dim, nx, tau, n_steps, param_map, fixed, prior_kind, prior_p0,
               prior_p1, step_space, solver=RD_SOLVER_AUTO, growth=0,
-              precision=None, w_max=100.0):
+              precision=None, w_max=100.0, rho_T=1.0):
     """Fills an rd_problem_desc (see include/rdbayes.h for each field)."""
     desc = rd_problem_desc()
     desc.dim = dim
@@ -178,7 +185,10 @@ def make_desc(dim, nx, tau, n_steps, param_map, fixed, prior_kind, prior_p0,
         desc.step_space[j] = step_space[j]
     for k in range(RD_NPARAM):
         desc.fixed[k] = fixed[k]
+    for k in range(3):  # p1..p3 of the polynomial growth law
+        desc.fixed_poly[k] = fixed[RD_NPARAM + k] if len(fixed) > RD_NPARAM + k else 0.0
     desc.w_max = w_max
+    desc.rho_T = rho_T
     return desc
 
 
@@ -224,8 +234,33 @@ def rd_evaluate_batch_noalloc(p, theta, loglik, status, size_idx=None, fields=No
                                             _dev_ptr(loglik), _dev_ptr(status), _dev_ptr(fields)))
 
 
+def rd_set_steady_state(p, threshold, confirm=False):
+    """Steady-state forward map: solve until the time derivative's L2 norm is
+    below threshold (0 = off), optionally confirmed at 2T."""
+    _check(load().rd_set_steady_state(p, float(threshold), 1 if confirm else 0))
+
+
+def rd_evaluate_batch_steady(p, theta, loglik, status, steps, size_idx=None, fields=None):
+    """rd_evaluate_batch in steady-state mode; steps: int32 CUDA tensor [B]
+    receives the step T at which each solve became stationary."""
+    _check(load().rd_evaluate_batch_steady(p, theta.shape[0], _dev_ptr(theta),
+                                           _dev_ptr(size_idx), _dev_ptr(loglik),
+                                           _dev_ptr(status), _dev_ptr(fields), _dev_ptr(steps)))
+
+
 def rd_set_scheme(p, scheme):
     _check(load().rd_set_scheme(p, scheme))
+
+
+def rd_set_wait_limit(p, seconds):
+    """Limit of the tensor-core solve kernels' bounded waits (default 4 s)."""
+    _check(load().rd_set_wait_limit(p, float(seconds)))
+
+
+def rd_debug_stall_at_step(p, step):
+    """Failure-path test aid: tensor-core issuers stall at IMEX step `step`
+    (-1 = off), so the launch ends with RD_ETIMEOUT after the wait limit."""
+    _check(load().rd_debug_stall_at_step(p, int(step)))
 
 
 def rd_set_turing_prior(p, enable=True):
@@ -236,6 +271,17 @@ def rd_set_size_kernel(p, size_idx, kernel):
     _check(load().rd_set_size_kernel(p, size_idx, kernel))
 
 
+def rd_set_size_schedule(p, size_idx, ctas_per_sm):
+    """Persistent CTAs per SM of that size's launch (0 = as many as fit)."""
+    _check(load().rd_set_size_schedule(p, size_idx, ctas_per_sm))
+
+
+def rd_get_size_schedule(p, size_idx):
+    k = ctypes.c_int(0)
+    _check(load().rd_get_size_schedule(p, size_idx, ctypes.byref(k)))
+    return k.value
+
+
 def rd_get_size_kernel(p, size_idx):
     k = ctypes.c_int(0)
     _check(load().rd_get_size_kernel(p, size_idx, ctypes.byref(k)))
@@ -243,11 +289,11 @@ def rd_get_size_kernel(p, size_idx):
 
 
 def rd_autotune(p, theta, n_trials=3, probe_steps=0, n_sizes=None):
-    """theta: host [B][P].  Returns [n_sizes][3] seconds per proposal (SIMT,
-    TC_STACKED, TC_RESIDENT; NaN where not applicable)."""
+    """theta: host [B][P].  Returns [n_sizes][4] seconds per proposal (SIMT,
+    TC_STACKED, TC_RESIDENT, CG; NaN where not applicable)."""
     th, pt = _host_ptr(theta, np.float64)
     ns = n_sizes if n_sizes is not None else RD_MAX_SIZES
-    out = np.full((RD_MAX_SIZES, 3), np.nan)
+    out = np.full((RD_MAX_SIZES, 4), np.nan)
     _check(load().rd_autotune(p, th.shape[0], pt, n_trials, probe_steps,
                               out.ctypes.data_as(ctypes.c_void_p)))
     return out[:ns]

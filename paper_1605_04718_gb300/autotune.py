@@ -15,13 +15,14 @@ import os
 
 import numpy as np
 
-from . import (RD_KERNEL_SIMT, RD_KERNEL_TC_RESIDENT, RD_KERNEL_TC_STACKED, rd_autotune,
-               rd_get_size_kernel, rd_set_size_kernel)
+from . import (RD_KERNEL_CG, RD_KERNEL_SIMT, RD_KERNEL_TC_RESIDENT, RD_KERNEL_TC_STACKED,
+               rd_autotune, rd_get_size_kernel, rd_get_size_schedule, rd_set_size_kernel,
+               rd_set_size_schedule)
 
 KERNEL_NAMES = {RD_KERNEL_SIMT: "simt", RD_KERNEL_TC_STACKED: "tc_stacked",
-                RD_KERNEL_TC_RESIDENT: "tc_resident"}
+                RD_KERNEL_TC_RESIDENT: "tc_resident", RD_KERNEL_CG: "cg"}
 _BY_NAME = {v: k for k, v in KERNEL_NAMES.items()}
-_COLUMNS = (RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT)
+_COLUMNS = (RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT, RD_KERNEL_CG)
 
 
 def cache_key(gpu: str, dim: int, n: int, n_steps: int) -> str:
@@ -55,15 +56,17 @@ def save_table(path: str, table: dict) -> None:
 
 def tune(p, gpu: str, dim: int, sizes, n_steps: int, theta, cache_path: str | None = None,
          n_trials: int = 3, probe_steps: int = 200, force: bool = False) -> dict:
-    """Sets the kernel of every size of problem ``p`` (grid sizes ``sizes``,
-    in size-index order) from the cache at ``cache_path`` when it has all of
-    them, else by ``rd_autotune`` on the probe batch ``theta`` (host
-    [B][n_params]) and writes the result back.  Returns {size_idx: entry}."""
+    """Sets the kernel and schedule (persistent CTAs per SM) of every size of
+    problem ``p`` (grid sizes ``sizes``, in size-index order) from the cache
+    at ``cache_path`` when it has all of them, else by ``rd_autotune`` on the
+    probe batch ``theta`` (host [B][n_params]) and writes the result back.
+    Returns {size_idx: entry}."""
     table = load_table(cache_path)
     keys = [cache_key(gpu, dim, n, n_steps) for n in sizes]
     if not force and all(k in table for k in keys):
         for s, k in enumerate(keys):
             rd_set_size_kernel(p, s, _BY_NAME[table[k]["kernel"]])
+            rd_set_size_schedule(p, s, int(table[k].get("ctas_per_sm", 0)))
         return {s: dict(table[k], cached=True) for s, k in enumerate(keys)}
     times = rd_autotune(p, np.asarray(theta, dtype=np.float64), n_trials=n_trials,
                         probe_steps=probe_steps, n_sizes=len(sizes))
@@ -71,7 +74,8 @@ def tune(p, gpu: str, dim: int, sizes, n_steps: int, theta, cache_path: str | No
     for s, (n, k) in enumerate(zip(sizes, keys)):
         kind = rd_get_size_kernel(p, s)
         assert kind == fastest(times[s])
-        entry = {"kernel": KERNEL_NAMES[kind], "n": int(n), "probe_steps": int(probe_steps),
+        entry = {"kernel": KERNEL_NAMES[kind], "ctas_per_sm": int(rd_get_size_schedule(p, s)),
+                 "n": int(n), "probe_steps": int(probe_steps),
                  "seconds_per_proposal": {KERNEL_NAMES[c]: (None if not math.isfinite(t) else t)
                                           for c, t in zip(_COLUMNS, times[s])}}
         table[k] = entry

@@ -51,7 +51,9 @@ WorkQueue make_queue(const rd_problem* p) {
 bool uses_tc(const rd_problem* p) {
   if (p->desc.dim != 2) return false;
   for (int s = 0; s < p->desc.n_sizes; ++s)
-    if (kernel_for_size(p, s) != RD_KERNEL_SIMT) return true;
+    if (kernel_for_size(p, s) == RD_KERNEL_TC_STACKED ||
+        kernel_for_size(p, s) == RD_KERNEL_TC_RESIDENT)
+      return true;
   return false;
 }
 
@@ -63,25 +65,49 @@ int kernel_for_size(const rd_problem* p, int s) {
   return p->desc.nx[s] == 128 ? RD_KERNEL_TC_RESIDENT : RD_KERNEL_TC_STACKED;
 }
 
+// Persistent CTAs of a kernel kind's launch when every SM holds as many as fit.
+static int grid_max_of(const rd_problem* p, int kind) {
+  switch (kind) {
+    case RD_KERNEL_TC_RESIDENT: return grid_solve_tc128(p->n_sm);
+    case RD_KERNEL_TC_STACKED: return grid_solve_tc(p->dev.max_n, p->n_sm);
+    case RD_KERNEL_CG: return grid_solve_cg(p->dev.max_n, false, p->n_sm);
+    default: return grid_solve_simt(p->desc.dim, p->dev.max_n, p->n_sm);
+  }
+}
+
 cudaError_t launch_solve_queue(rd_problem* p, const WorkQueue& q, const double* theta,
-                               double* phi, uint32_t* status, void* fields, cudaStream_t st) {
-  static const int kinds[3] = {RD_KERNEL_TC_RESIDENT, RD_KERNEL_TC_STACKED, RD_KERNEL_SIMT};
+                               double* phi, uint32_t* status, void* fields, cudaStream_t st,
+                               int* steps_out) {
+  if (p->dev.ss_tol > 0.0)  // steady-state mode: every size, CUDA cores, one launch
+    return launch_solve_simt(p->dev, q, theta, phi, status, fields,
+                             grid_solve_simt(p->desc.dim, p->dev.max_n, p->n_sm, true), st,
+                             steps_out);
+  if (p->desc.dim == 2 && p->dev.scheme == RD_SCHEME_PICARD)  // every size: one launch
+    return launch_solve_cg(p->dev, q, theta, phi, status, fields, true,
+                           grid_solve_cg(p->dev.max_n, true, p->n_sm), st);
+  static const int kinds[4] = {RD_KERNEL_TC_RESIDENT, RD_KERNEL_TC_STACKED, RD_KERNEL_SIMT,
+                               RD_KERNEL_CG};
   for (int kind : kinds) {
     WorkQueue sub = q;  // the sizes of this kernel, largest grid first
     sub.n_sizes = 0;
+    int want = 0;  // CTAs per SM: the largest any of these sizes asks for
     for (int k = 0; k < q.n_sizes; ++k)
-      if (kernel_for_size(p, q.order[k]) == kind) sub.order[sub.n_sizes++] = q.order[k];
+      if (kernel_for_size(p, q.order[k]) == kind) {
+        sub.order[sub.n_sizes++] = q.order[k];
+        want = std::max(want, p->ctas_per_sm[q.order[k]]);
+      }
     if (sub.n_sizes == 0) continue;
+    const int gmax = grid_max_of(p, kind);
+    const int grid = (want > 0 && want * p->n_sm < gmax) ? want * p->n_sm : gmax;
     cudaError_t e;
     if (kind == RD_KERNEL_TC_RESIDENT)
-      e = launch_solve_tc128(p->dev, sub, theta, phi, status, fields, grid_solve_tc128(p->n_sm),
-                             p->ws.err, st);
+      e = launch_solve_tc128(p->dev, sub, theta, phi, status, fields, grid, p->ws.err, st);
     else if (kind == RD_KERNEL_TC_STACKED)
-      e = launch_solve_tc(p->dev, sub, theta, phi, status, fields,
-                          grid_solve_tc(p->dev.max_n, p->n_sm), p->ws.err, st);
+      e = launch_solve_tc(p->dev, sub, theta, phi, status, fields, grid, p->ws.err, st);
+    else if (kind == RD_KERNEL_CG)
+      e = launch_solve_cg(p->dev, sub, theta, phi, status, fields, false, grid, st);
     else
-      e = launch_solve_simt(p->dev, sub, theta, phi, status, fields,
-                            grid_solve_simt(p->desc.dim, p->dev.max_n, p->n_sm), st);
+      e = launch_solve_simt(p->dev, sub, theta, phi, status, fields, grid, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -133,8 +159,15 @@ static rd_status validate_desc(const rd_problem_desc* d) {
            RD_EINVAL, "solver not available for this dimension");
   RD_CHECK(d->n_params >= 1 && d->n_params <= RD_NPARAM, RD_EINVAL,
            "n_params must be in 1..5");
+  RD_CHECK(d->growth >= RD_GROWTH_NONE && d->growth <= RD_GROWTH_POLY4, RD_EINVAL,
+           "unknown growth law");
+  RD_CHECK(d->growth != RD_GROWTH_POLY4 || d->dim == 1, RD_EINVAL,
+           "the polynomial growth law is built for 1-D problems");
+  RD_CHECK(d->growth != RD_GROWTH_POLY4 || (d->rho_T > 0 && isfinite(d->rho_T)), RD_EINVAL,
+           "the polynomial growth law needs rho_T > 0");
   for (int j = 0; j < d->n_params; ++j) {
-    RD_CHECK(d->param_map[j] >= 0 && d->param_map[j] < RD_NPARAM, RD_EINVAL,
+    const int hi = d->growth == RD_GROWTH_POLY4 ? RD_NPHYS : RD_NPARAM;
+    RD_CHECK(d->param_map[j] >= 0 && d->param_map[j] < hi, RD_EINVAL,
              "param_map entry out of range");
     for (int k = 0; k < j; ++k)
       RD_CHECK(d->param_map[k] != d->param_map[j], RD_EINVAL, "param_map repeats a parameter");
@@ -180,6 +213,13 @@ rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
     set_error("cannot query the CUDA device");
     return RD_ECUDA;
   }
+  {
+    const rd_status ns = noalloc_prepare(p->device);
+    if (ns != RD_OK) {
+      delete p;
+      return ns;
+    }
+  }
   DevProblem& dv = p->dev;
   memset(&dv, 0, sizeof(dv));
   dv.dim = desc->dim;
@@ -190,6 +230,8 @@ rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
   dv.n_params = desc->n_params;
   dv.tau = desc->tau;
   dv.w_max = p->desc.w_max;
+  dv.wait_ns = 4000000000ull;
+  dv.stall_step = -1;
   for (int j = 0; j < kNParam; ++j) {
     dv.param_map[j] = desc->param_map[j];
     dv.fixed[j] = desc->fixed[j];
@@ -198,6 +240,8 @@ rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
     dv.prior_p1[j] = desc->prior_p1[j];
     dv.step_space[j] = desc->step_space[j];
   }
+  for (int j = 0; j < 3; ++j) dv.fixed[kNParam + j] = desc->fixed_poly[j];
+  dv.rho_T = desc->rho_T;
   dv.max_n = 0;
   const double pi = 3.14159265358979323846264338327950288;
   for (int s = 0; s < desc->n_sizes; ++s) {
@@ -241,6 +285,8 @@ rd_status rd_problem_create(const rd_problem_desc* desc, void* cuda_stream,
   for (int k = 0; k < desc->n_sizes; ++k) has128 = has128 || (desc->dim == 2 && desc->nx[k] == 128);
   if (setup_solve_simt(desc->dim, dv.max_n) != cudaSuccess ||
       (desc->dim == 2 && setup_solve_tc(dv.max_n) != cudaSuccess) ||
+      (desc->dim == 2 && cg_applicable(dv.max_n, false) &&
+       setup_solve_cg(dv.max_n, false) != cudaSuccess) ||
       (has128 && setup_solve_tc128() != cudaSuccess)) {
     rd_problem_destroy(p);
     set_error("cannot configure the solve kernels' shared memory");
@@ -359,9 +405,12 @@ rd_status rd_set_observations(rd_problem* p, int size_idx, int n_times,
 }
 
 static rd_status check_ready(rd_problem* p) {
-  for (int s = 0; s < p->desc.n_sizes; ++s)
+  for (int s = 0; s < p->desc.n_sizes; ++s) {
     RD_CHECK(p->ic_set[s] && p->obs_set[s], RD_ESTATE,
              "initial state and observations must be set for every grid size");
+    RD_CHECK(p->dev.ss_tol <= 0.0 || p->dev.sz[s].n_obs == 1, RD_ESTATE,
+             "steady-state mode observes once: set exactly one observation time");
+  }
   return RD_OK;
 }
 
@@ -381,12 +430,46 @@ rd_status rd_evaluate_batch(rd_problem* p, int B, const double* theta,
   return RD_OK;
 }
 
+rd_status rd_set_steady_state(rd_problem* p, double threshold, int confirm) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(threshold >= 0.0 && isfinite(threshold), RD_EINVAL, "threshold must be >= 0");
+  if (threshold > 0.0) {
+    RD_CHECK(!p->desc.growth, RD_EINVAL, "steady states are sought on a fixed domain");
+    RD_CHECK(p->desc.dim == 1 || p->dev.max_n <= 96, RD_EINVAL,
+             "steady-state mode in 2-D needs every grid at N <= 96");
+    RD_CUDA(setup_solve_simt(p->desc.dim, p->dev.max_n, true));
+  }
+  p->dev.ss_tol = threshold;
+  p->dev.ss_confirm = confirm ? 1 : 0;
+  ++p->generation;  // captured chain steps hold the problem by value
+  return RD_OK;
+}
+
+rd_status rd_evaluate_batch_steady(rd_problem* p, int B, const double* theta,
+                                   const int* size_idx, double* loglik, uint32_t* status,
+                                   void* fields, int* steps) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(p->dev.ss_tol > 0.0, RD_ESTATE, "steady-state mode is off (rd_set_steady_state)");
+  RD_CHECK(B >= 0, RD_EINVAL, "B must be >= 0");
+  if (B == 0) return RD_OK;
+  RD_CHECK(theta && loglik && status, RD_EINVAL, "NULL argument");
+  rd_status r = check_ready(p);
+  if (r != RD_OK) return r;
+  if ((r = ensure_capacity(p, B)) != RD_OK) return r;
+  WorkQueue q = make_queue(p);
+  RD_CUDA(launch_fill_queue(q, B, size_idx, loglik, status, p->stream));
+  RD_CUDA(launch_solve_queue(p, q, theta, loglik, status, fields, p->stream, steps));
+  return RD_OK;
+}
+
 rd_status rd_set_size_kernel(rd_problem* p, int size_idx, int kernel) {
   RD_CHECK(p, RD_EINVAL, "problem is NULL");
   RD_CHECK(p->desc.dim == 2, RD_EINVAL, "1-D problems always use the Thomas solve");
   RD_CHECK(size_idx >= 0 && size_idx < p->desc.n_sizes, RD_EINVAL, "size_idx out of range");
-  RD_CHECK(kernel >= RD_KERNEL_DEFAULT && kernel <= RD_KERNEL_TC_RESIDENT, RD_EINVAL,
+  RD_CHECK(kernel >= RD_KERNEL_DEFAULT && kernel <= RD_KERNEL_CG, RD_EINVAL,
            "unknown kernel");
+  RD_CHECK(kernel != RD_KERNEL_CG || cg_applicable(p->dev.max_n, false), RD_EINVAL,
+           "RD_KERNEL_CG needs every grid of the problem at N <= 96");
   RD_CHECK(kernel != RD_KERNEL_TC_RESIDENT || p->desc.nx[size_idx] == 128, RD_EINVAL,
            "RD_KERNEL_TC_RESIDENT needs N = 128");
   if (p->kernel_of_size[size_idx] != kernel) {
@@ -399,8 +482,10 @@ rd_status rd_set_size_kernel(rd_problem* p, int size_idx, int kernel) {
 rd_status rd_set_scheme(rd_problem* p, int scheme) {
   RD_CHECK(p, RD_EINVAL, "problem is NULL");
   RD_CHECK(scheme == RD_SCHEME_IMEX || scheme == RD_SCHEME_PICARD, RD_EINVAL, "unknown scheme");
-  RD_CHECK(scheme == RD_SCHEME_IMEX || p->desc.dim == 1, RD_EINVAL,
-           "the semi-implicit scheme is built for 1-D problems");
+  RD_CHECK(scheme == RD_SCHEME_IMEX || p->desc.dim == 1 || cg_applicable(p->dev.max_n, true),
+           RD_EINVAL, "the semi-implicit scheme in 2-D needs every grid at N <= 80");
+  if (scheme == RD_SCHEME_PICARD && p->desc.dim == 2)
+    RD_CUDA(setup_solve_cg(p->dev.max_n, true));
   p->dev.scheme = scheme;
   ++p->generation;  // captured chain steps hold the problem by value
   return RD_OK;
@@ -410,6 +495,43 @@ rd_status rd_set_turing_prior(rd_problem* p, int enable) {
   RD_CHECK(p, RD_EINVAL, "problem is NULL");
   p->dev.turing = enable ? 1 : 0;
   ++p->generation;  // captured chain steps hold the problem by value
+  return RD_OK;
+}
+
+rd_status rd_set_wait_limit(rd_problem* p, double seconds) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(seconds > 0 && seconds <= 60.0, RD_EINVAL, "wait limit must be in (0, 60] seconds");
+  const unsigned long long ns = (unsigned long long)(seconds * 1e9);
+  p->dev.wait_ns = ns > 0 ? ns : 1ull;
+  ++p->generation;  // captured chain steps hold the problem by value
+  return RD_OK;
+}
+
+rd_status rd_debug_stall_at_step(rd_problem* p, int step) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(step >= -1, RD_EINVAL, "step must be >= -1");
+  p->dev.stall_step = step;
+  ++p->generation;  // captured chain steps hold the problem by value
+  return RD_OK;
+}
+
+rd_status rd_set_size_schedule(rd_problem* p, int size_idx, int ctas_per_sm) {
+  RD_CHECK(p, RD_EINVAL, "problem is NULL");
+  RD_CHECK(size_idx >= 0 && size_idx < p->desc.n_sizes, RD_EINVAL, "size_idx out of range");
+  RD_CHECK(ctas_per_sm >= 0 && ctas_per_sm <= 32, RD_EINVAL, "ctas_per_sm must be in 0..32");
+  if (p->ctas_per_sm[size_idx] != ctas_per_sm) {
+    p->ctas_per_sm[size_idx] = ctas_per_sm;
+    ++p->generation;  // captured chain steps hold the old launches
+  }
+  return RD_OK;
+}
+
+rd_status rd_get_size_schedule(const rd_problem* p, int size_idx, int* ctas_per_sm) {
+  RD_CHECK(p && ctas_per_sm, RD_EINVAL, "NULL argument");
+  RD_CHECK(size_idx >= 0 && size_idx < p->desc.n_sizes, RD_EINVAL, "size_idx out of range");
+  const int gmax = grid_max_of(p, kernel_for_size(p, size_idx)) / p->n_sm;
+  const int want = p->ctas_per_sm[size_idx];
+  *ctas_per_sm = (want > 0 && want < gmax) ? want : gmax;
   return RD_OK;
 }
 
@@ -456,8 +578,7 @@ rd_status rd_evaluate_batch_host(rd_problem* p, int B, const double* theta,
                           cudaMemcpyDeviceToHost, p->stream));
   RD_CUDA(cudaMemcpyAsync(status, p->d2h_status, sizeof(uint32_t) * (size_t)B,
                           cudaMemcpyDeviceToHost, p->stream));
-  RD_CUDA(cudaStreamSynchronize(p->stream));
-  return RD_OK;
+  return rd_sync(p);  // waits, then reports a bounded wait that gave up
 }
 
 rd_status rd_sync(rd_problem* p) {
@@ -484,16 +605,20 @@ rd_status rd_autotune(rd_problem* p, int B, const double* theta, int n_trials, i
   if (r != RD_OK) return r;
   if ((r = ensure_capacity(p, B)) != RD_OK) return r;
   const int P = p->desc.n_params, ns = p->desc.n_sizes;
-  static const int kinds[3] = {RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT};
-  double times[RD_MAX_SIZES][3];
+  static const int kinds[4] = {RD_KERNEL_SIMT, RD_KERNEL_TC_STACKED, RD_KERNEL_TC_RESIDENT,
+                               RD_KERNEL_CG};
+  double times[RD_MAX_SIZES][4];
   double* d_theta = nullptr;
   double* d_phi = nullptr;
   uint32_t* d_st = nullptr;
   int* d_size = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const int saved_steps = p->dev.n_steps;
-  int saved_kernel[RD_MAX_SIZES];
-  for (int s = 0; s < RD_MAX_SIZES; ++s) saved_kernel[s] = p->kernel_of_size[s];
+  int saved_kernel[RD_MAX_SIZES], saved_ctas[RD_MAX_SIZES];
+  for (int s = 0; s < RD_MAX_SIZES; ++s) {
+    saved_kernel[s] = p->kernel_of_size[s];
+    saved_ctas[s] = p->ctas_per_sm[s];
+  }
   std::string fail;
   auto cu = [&](cudaError_t e, const char* what) {
     if (e != cudaSuccess && fail.empty()) fail = std::string(what) + ": " + cudaGetErrorString(e);
@@ -514,11 +639,17 @@ rd_status rd_autotune(rd_problem* p, int B, const double* theta, int n_trials, i
     ok = cu(cudaMemcpyAsync(d_size, sizes.data(), sizeof(int) * (size_t)B, cudaMemcpyHostToDevice,
                             p->stream), "cudaMemcpyAsync") &&
          cu(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
-    int best = -1;
-    for (int k = 0; ok && k < 3; ++k) {
+    int best = -1, best_ctas = 0;
+    double best_t = INFINITY;
+    for (int k = 0; ok && k < 4; ++k) {
       times[s][k] = NAN;
       if (kinds[k] == RD_KERNEL_TC_RESIDENT && p->desc.nx[s] != 128) continue;
+      if (kinds[k] == RD_KERNEL_CG && !cg_applicable(p->dev.max_n, false)) continue;
       p->kernel_of_size[s] = kinds[k];
+      // schedule axis: 1, 2, 4, ... persistent CTAs per SM up to what fits
+      const int per_max = std::max(1, grid_max_of(p, kinds[k]) / p->n_sm);
+      for (int ctas = 1; ok && ctas <= per_max; ctas *= 2) {
+      p->ctas_per_sm[s] = ctas;
       std::vector<float> ms;
       for (int t = 0; ok && t <= n_trials; ++t) {  // trial 0 warms up
         const WorkQueue q = make_queue(p);
@@ -540,13 +671,25 @@ rd_status rd_autotune(rd_problem* p, int B, const double* theta, int n_trials, i
       }
       if (!ok) break;
       std::sort(ms.begin(), ms.end());
-      times[s][k] = 1e-3 * (double)ms[ms.size() / 2] / B;  // seconds per proposal
-      if (best < 0 || times[s][k] < times[s][best]) best = k;
+      const double t_sec = 1e-3 * (double)ms[ms.size() / 2] / B;  // seconds per proposal
+      if (!(times[s][k] <= t_sec)) times[s][k] = t_sec;  // best schedule of this kind
+      if (t_sec < best_t) {
+        best_t = t_sec;
+        best = k;
+        best_ctas = ctas;
+      }
+      }
     }
-    if (ok) saved_kernel[s] = kinds[best];
+    if (ok) {
+      saved_kernel[s] = kinds[best];
+      saved_ctas[s] = best_ctas;
+    }
   }
   p->dev.n_steps = saved_steps;
-  for (int s = 0; s < RD_MAX_SIZES; ++s) p->kernel_of_size[s] = saved_kernel[s];
+  for (int s = 0; s < RD_MAX_SIZES; ++s) {
+    p->kernel_of_size[s] = saved_kernel[s];
+    p->ctas_per_sm[s] = saved_ctas[s];
+  }
   ++p->generation;  // captured chain steps hold the old launches
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -560,7 +703,7 @@ rd_status rd_autotune(rd_problem* p, int B, const double* theta, int n_trials, i
   }
   if (times_out)
     for (int s = 0; s < ns; ++s)
-      for (int k = 0; k < 3; ++k) times_out[3 * s + k] = times[s][k];
+      for (int k = 0; k < 4; ++k) times_out[4 * s + k] = times[s][k];
   return RD_OK;
 }
 

@@ -12,6 +12,7 @@ namespace rd {
 constexpr int kMaxSizes = RD_MAX_SIZES;
 constexpr int kMaxObs = RD_MAX_OBS;
 constexpr int kNParam = RD_NPARAM;
+constexpr int kNPhys = RD_NPHYS;
 
 // One grid size of a problem: its initial state, observations and the
 // constant tables of its implicit solve.
@@ -43,8 +44,13 @@ struct DevProblem {
   int max_n;
   double tau;
   double w_max;
+  unsigned long long wait_ns;  // limit of the solve kernels' bounded waits
+  int stall_step;  // >= 0: tensor-core issuers stall at this step (failure-path test aid)
+  double ss_tol;   // > 0: solve to a steady state (time-derivative L2 norm below this)
+  int ss_confirm;  // steady state: also require |w(2T) - w(T)| < ss_tol
   int param_map[kNParam];
-  double fixed[kNParam];
+  double fixed[kNPhys];   // model parameters not inferred
+  double rho_T;           // RD_GROWTH_POLY4: rho(T)
   int prior_kind[kNParam];
   double prior_p0[kNParam];
   double prior_p1[kNParam];
@@ -66,13 +72,62 @@ struct WorkQueue {
   int n_sizes;
 };
 
-// Full parameter vector (a, b, d, gamma, r) of inferred values th[0..P).
+// Full model parameter vector (a, b, d, gamma, r, p1, p2, p3) of inferred
+// values th[0..P).
 __device__ __forceinline__ void full_theta(const DevProblem& pb,
-                                           const double* th, double out[5]) {
+                                           const double* th, double out[kNPhys]) {
 #pragma unroll
-  for (int i = 0; i < kNParam; ++i) out[i] = pb.fixed[i];
+  for (int i = 0; i < kNPhys; ++i) out[i] = pb.fixed[i];
   for (int j = 0; j < pb.n_params; ++j) out[pb.param_map[j]] = th[j];
-  if (!pb.growth) out[4] = 0.0;
+  if (pb.growth != RD_GROWTH_EXP) out[4] = 0.0;
+}
+
+// rho(t) and rho'(t) / rho(t) of the problem's growth law at time t (FP64;
+// T = n_steps tau for the polynomial law of Example 1).
+__device__ __forceinline__ void growth_at(const DevProblem& pb, const double th[kNPhys],
+                                          double t, double& rho, double& q) {
+  if (pb.growth == RD_GROWTH_POLY4) {
+    const double T = (double)pb.n_steps * pb.tau;
+    const double p1 = th[5], p2 = th[6], p3 = th[7];
+    const double p4 = pb.rho_T - 1.0 - p1 - p2 - p3;
+    const double s = t / T;
+    rho = 1.0 + s * (p1 + s * (p2 + s * (p3 + s * p4)));
+    q = (p1 + s * (2.0 * p2 + s * (3.0 * p3 + s * 4.0 * p4))) / T / rho;
+  } else {
+    rho = exp(th[4] * t);
+    q = th[4];
+  }
+}
+
+// growth_at with explicitly rounded FP64 operations (no fused multiply-add),
+// in the order written, for the bit-reproducible semi-implicit step.
+__device__ __forceinline__ void growth_at_rn(const DevProblem& pb, const double th[kNPhys],
+                                             double t, double& rho, double& q) {
+  if (pb.growth == RD_GROWTH_POLY4) {
+    const double T = __dmul_rn((double)pb.n_steps, pb.tau);
+    const double p1 = th[5], p2 = th[6], p3 = th[7];
+    const double p4 = __dsub_rn(__dsub_rn(__dsub_rn(__dsub_rn(pb.rho_T, 1.0), p1), p2), p3);
+    const double s = __ddiv_rn(t, T);
+    rho = __dadd_rn(1.0, __dmul_rn(s, __dadd_rn(p1, __dmul_rn(s, __dadd_rn(p2,
+              __dmul_rn(s, __dadd_rn(p3, __dmul_rn(s, p4))))))));
+    const double drds = __dadd_rn(p1, __dmul_rn(s, __dadd_rn(__dmul_rn(2.0, p2),
+              __dmul_rn(s, __dadd_rn(__dmul_rn(3.0, p3), __dmul_rn(__dmul_rn(s, 4.0), p4))))));
+    q = __ddiv_rn(__ddiv_rn(drds, T), rho);
+  } else {
+    rho = exp(__dmul_rn(th[4], t));
+    q = th[4];
+  }
+}
+
+// Support of the polynomial growth law: rho > 0 at s = k / 1000, k = 0..1000.
+__device__ __forceinline__ bool poly4_positive(const DevProblem& pb, const double th[kNPhys]) {
+  const double p1 = th[5], p2 = th[6], p3 = th[7];
+  const double p4 = pb.rho_T - 1.0 - p1 - p2 - p3;
+  for (int k = 0; k <= 1000; ++k) {
+    const double s = (double)k / 1000.0;
+    if (!(1.0 + s * (p1 + s * (p2 + s * (p3 + s * p4))) > 0.0)) return false;
+  }
+  return true;
 }
 
 // Pops the next work item; returns the proposal index or -1 when every list

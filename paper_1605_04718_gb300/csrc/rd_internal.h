@@ -14,6 +14,9 @@
 namespace rd {
 
 void set_error(const std::string& msg);
+// Looks up (once per device, that device current) the device address of the
+// fixed scratch of rd_evaluate_batch_noalloc (rd_noalloc.cu).
+rd_status noalloc_prepare(int device);
 
 // Problem-level device workspace: work lists and per-proposal outputs of the
 // chain sampler's exact solves.
@@ -45,6 +48,8 @@ struct rd_problem {
   int generation = 0;
   // RD_KERNEL_* of each size; RD_KERNEL_DEFAULT follows desc.solver
   int kernel_of_size[RD_MAX_SIZES] = {0, 0, 0, 0};
+  // persistent CTAs per SM of each size's launch (0 = the kernel's maximum)
+  int ctas_per_sm[RD_MAX_SIZES] = {0, 0, 0, 0};
   // staging for rd_evaluate_batch_host
   double* h2d_theta = nullptr;
   int* h2d_size = nullptr;
@@ -93,10 +98,13 @@ namespace rd {
 
 cudaError_t launch_fill_queue(const WorkQueue& q, int B, const int* size_idx,
                               double* phi, uint32_t* status, cudaStream_t st);
+// CUDA-core kernels (rd_solve_simt.cu); steady: the steady-state-mode variant
+// (pb.ss_tol > 0), whose steps_out (may be null) receives each proposal's T.
 cudaError_t launch_solve_simt(const DevProblem& pb, const WorkQueue& q,
                               const double* theta, double* phi, uint32_t* status,
-                              void* fields, int grid, cudaStream_t st);
-cudaError_t setup_solve_simt(int dim, int max_n);
+                              void* fields, int grid, cudaStream_t st,
+                              int* steps_out = nullptr);
+cudaError_t setup_solve_simt(int dim, int max_n, bool steady = false);
 cudaError_t setup_solve_tc(int max_n);
 int grid_solve_tc(int max_n, int n_sm);
 cudaError_t launch_solve_tc(const DevProblem& pb, const WorkQueue& q, const double* theta,
@@ -111,16 +119,26 @@ int grid_solve_tc128(int n_sm);
 cudaError_t launch_solve_tc128(const DevProblem& pb, const WorkQueue& q, const double* theta,
                                double* phi, uint32_t* status, void* fields, int grid, int* err,
                                cudaStream_t st);
+// CUDA-core conjugate-gradient solves (rd_solve_simt.cu): the IMEX step by
+// plain CG (RD_KERNEL_CG, N <= 96) or the paper's semi-implicit step by
+// preconditioned CG (picard, N <= 80).
+bool cg_applicable(int n, bool picard);
+cudaError_t setup_solve_cg(int max_n, bool picard);
+int grid_solve_cg(int max_n, bool picard, int n_sm);
+cudaError_t launch_solve_cg(const DevProblem& pb, const WorkQueue& q, const double* theta,
+                            double* phi, uint32_t* status, void* fields, bool picard, int grid,
+                            cudaStream_t st);
 bool uses_tc(const rd_problem* p);
-int grid_solve_simt(int dim, int max_n, int n_sm);
-size_t simt2d_smem_bytes(int n);
+int grid_solve_simt(int dim, int max_n, int n_sm, bool steady = false);
+size_t simt2d_smem_bytes(int n, bool steady = false);
 
 WorkQueue make_queue(const rd_problem* p);
 int kernel_for_size(const rd_problem* p, int size_idx);
 // Launches the solve kernels over the queue's sizes, one persistent launch
 // per kernel kind in use (sizes grouped by kernel_for_size).
 cudaError_t launch_solve_queue(rd_problem* p, const WorkQueue& q, const double* theta,
-                               double* phi, uint32_t* status, void* fields, cudaStream_t st);
+                               double* phi, uint32_t* status, void* fields, cudaStream_t st,
+                               int* steps_out = nullptr);
 cudaError_t launch_solve(rd_problem* p, const double* theta, double* phi,
                          uint32_t* status, void* fields);
 

@@ -83,7 +83,7 @@ static ChainView view_of(const rd_chains* c) {
 // d f_u + g_v > 0, (d f_u + g_v)^2 - 4 d (f_u g_v - f_v g_u) > 0 with
 // f_u = (b - a)/(b + a), g_v = -(a + b)^2, f_u g_v - f_v g_u = (a + b)^2.
 __device__ bool in_turing_space(const DevProblem& pb, const double* th) {
-  double full[kNParam];
+  double full[kNPhys];
   full_theta(pb, th, full);
   const double a = full[0], b = full[1], d = full[2];
   const double s = a + b;
@@ -115,6 +115,11 @@ __device__ double log_prior_eta(const DevProblem& pb, const double* th) {
     lp += lpj;
   }
   if (pb.turing && !in_turing_space(pb, th)) lp = -(double)INFINITY;
+  if (pb.growth == RD_GROWTH_POLY4 && isfinite(lp)) {
+    double full[kNPhys];
+    full_theta(pb, th, full);
+    if (!poly4_positive(pb, full)) lp = -(double)INFINITY;
+  }
   return lp;
 }
 
@@ -142,6 +147,8 @@ __global__ void k_chain_init(DevProblem pb, WorkQueue q, ChainView v) {
   const double lp = log_prior_eta(pb, th);
   v.lp[c] = lp;
   if (isfinite(lp)) {
+    v.phi[c] = (double)INFINITY;  // pending until the solve writes it
+    v.prop_status[c] = RD_P_NOT_SOLVED;
     queue_push(q, v.size_idx[c], c);
   } else {
     v.phi[c] = (double)INFINITY;
@@ -177,7 +184,11 @@ __global__ void k_chain_propose(DevProblem pb, WorkQueue q, ChainView v, int pus
   v.prop_lp[c] = lp;
   if (isfinite(lp)) {
     v.prop_status[c] = 0u;
-    if (push) queue_push(q, v.size_idx[c], c);
+    if (push) {  // pending until the solve writes Phi and the status
+      v.prop_status[c] = RD_P_NOT_SOLVED;
+      v.prop_phi[c] = (double)INFINITY;
+      queue_push(q, v.size_idx[c], c);
+    }
   } else {
     v.prop_status[c] = RD_P_OUT_OF_SUPPORT;
     v.prop_phi[c] = (double)INFINITY;
@@ -195,6 +206,8 @@ __global__ void k_chain_stage1(WorkQueue q, ChainView v) {
   chain_uniforms(v.seed, v.first + (uint32_t)c, (uint32_t)v.ctl[0], u);
   const double la1 = (-v.prop_phit[c] + v.prop_lp[c]) - (-v.phit[c] + v.lp[c]);
   if (log(u[6]) < la1) {
+    v.prop_status[c] = RD_P_NOT_SOLVED;  // pending until the solve writes it
+    v.prop_phi[c] = (double)INFINITY;
     queue_push(q, v.size_idx[c], c);
   } else {
     v.prop_status[c] = kStage1Reject;
@@ -287,7 +300,8 @@ __global__ void k_pmh_propose(DevProblem pb, WorkQueue q, ChainView v) {
   const double lp = log_prior_eta(pb, th);
   v.pmh_lp[i] = lp;
   if (isfinite(lp)) {
-    v.pmh_status[i] = 0u;
+    v.pmh_status[i] = RD_P_NOT_SOLVED;  // pending until the solve writes it
+    v.pmh_phi[i] = (double)INFINITY;
     queue_push(q, v.size_idx[c], i);
   } else {
     v.pmh_status[i] = RD_P_OUT_OF_SUPPORT;

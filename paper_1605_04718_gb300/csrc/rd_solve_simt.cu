@@ -17,6 +17,7 @@
 
 #include "rd_common.cuh"
 #include "rd_internal.h"
+#include "rd_simt_common.cuh"
 #include "rd_tc_ptx.cuh"
 
 namespace rd {
@@ -41,12 +42,20 @@ __device__ __forceinline__ void thomas_factors(int n, double alpha, double beta,
   }
 }
 
+// Steady-state mode (pb.ss_tol > 0, fixed domain, Sec. 3.1.2): the step loop
+// stops at the first step T whose discrete time derivative has
+//   (h^dim sum over both fields ((w^{T} - w^{T-1}) / tau)^2)^(1/2) < ss_tol,
+// at most n_steps; the single observation is taken at T.  With ss_confirm the
+// solve goes on to 2T and requires (h^dim sum (w(2T) - w(T))^2)^(1/2) < ss_tol;
+// the reported state stays w(T).  Either failure is RD_P_NOT_CONVERGED.
+// steps_out (may be null) receives T (0 when none was reached).
 template <int NMAX>
 __device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
-                             const double th[5], double* phi_out,
-                             uint32_t* st_out, double* fields_out) {
+                             const double th[kNPhys], double* phi_out,
+                             uint32_t* st_out, double* fields_out, int* steps_out) {
   double u[NMAX], v[NMAX], ru[NMAX], rv[NMAX];
   double cu[NMAX], cv[NMAX], iu[NMAX], iv[NMAX];
+  double up[NMAX], vp[NMAX];  // steady-state mode: previous step, then w(T)
   const int n = S.n;
   for (int i = 0; i < n; ++i) {
     u[i] = S.u0d[i];
@@ -55,43 +64,74 @@ __device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
   const double a = th[0], b = th[1], d = th[2], g = th[3], r = th[4];
   const double tau = pb.tau, h2inv = (double)n * n, tg = tau * g;
   const int nfo = (S.field_mask & 1) + ((S.field_mask >> 1) & 1);
-  const bool grow = (r != 0.0);
+  const bool grow = (r != 0.0) || pb.growth == RD_GROWTH_POLY4;
   double phi = 0.0;
   bool bad = false;
   int next_obs = 0;
   double alpha = 1.0, bu = tau * h2inv, bv = tau * d * h2inv;
   thomas_factors<NMAX>(n, alpha, bu, cu, iu);
   thomas_factors<NMAX>(n, alpha, bv, cv, iv);
-  for (int step = 0; step < pb.n_steps; ++step) {
+  const bool steady = pb.ss_tol > 0.0;
+  int t_ss = 0, phase = 0;  // steady state: 0 seek T, 1 confirm to 2T
+  bool conv = !steady;
+  for (int step = 0; steady || step < pb.n_steps; ++step) {
+    if (steady) {
+      if (phase == 0 && step >= pb.n_steps) break;
+      if (phase == 0)
+        for (int i = 0; i < n; ++i) {
+          up[i] = u[i];
+          vp[i] = v[i];
+        }
+    }
     if (pb.scheme == RD_SCHEME_PICARD) {
       // the paper's semi-implicit step: the reaction linearised with u^n, v^n
       // and implicit, so the diagonal varies by node (Thomas, eliminated in
-      // place: cu / cv hold c'_i, ru / rv hold d'_i)
-      const double rho = exp(r * (double)step * tau);
-      const double al = 1.0 + tau * 1.0 * r;  // m = 1 in 1-D
-      const double bu1 = tau / (rho * rho) * h2inv, bv1 = tau * d / (rho * rho) * h2inv;
+      // place: cu / cv hold c'_i, ru / rv hold d'_i).  Every operation is an
+      // explicitly rounded FP64 one (no fused multiply-add) in a fixed order:
+      // on a growing domain at large gamma the pattern reached after millions
+      // of steps depends on the rounding of each step, so the step is kept
+      // reproducible to the bit.
+      double rho, q;  // rho_n and rho'/rho at t_n, FP64
+      growth_at_rn(pb, th, __dmul_rn((double)step, tau), rho, q);
+      if (!(rho > 0.0)) {
+        bad = true;
+        break;
+      }
+      const double al = __dadd_rn(1.0, __dmul_rn(__dmul_rn(tau, 1.0), q));  // m = 1 in 1-D
+      const double h = __ddiv_rn(1.0, (double)n), hh = __dmul_rn(h, h);
+      const double rr = __dmul_rn(rho, rho);
+      const double bu1 = __ddiv_rn(__ddiv_rn(__dmul_rn(tau, 1.0), rr), hh);
+      const double bv1 = __ddiv_rn(__ddiv_rn(__dmul_rn(tau, d), rr), hh);
       for (int i = 0; i < n; ++i) {
-        const double aui = al + tg * (1.0 - u[i] * v[i]);
-        const double avi = al + tg * u[i] * u[i];
-        const double rU = u[i] + tg * a, rV = v[i] + tg * b;
+        const double aui = __dadd_rn(al, __dmul_rn(tg, __dsub_rn(1.0, __dmul_rn(u[i], v[i]))));
+        const double avi = __dadd_rn(al, __dmul_rn(__dmul_rn(tg, u[i]), u[i]));
+        const double rU = __dadd_rn(u[i], __dmul_rn(tg, a));
+        const double rV = __dadd_rn(v[i], __dmul_rn(tg, b));
         const double edge = (i == 0 || i == n - 1) ? 1.0 : 2.0;
-        const double du = aui + edge * bu1 + (i > 0 ? bu1 * cu[i - 1] : 0.0);
-        const double dv = avi + edge * bv1 + (i > 0 ? bv1 * cv[i - 1] : 0.0);
-        cu[i] = (i < n - 1) ? -bu1 / du : 0.0;
-        cv[i] = (i < n - 1) ? -bv1 / dv : 0.0;
-        ru[i] = (rU + (i > 0 ? bu1 * ru[i - 1] : 0.0)) / du;
-        rv[i] = (rV + (i > 0 ? bv1 * rv[i - 1] : 0.0)) / dv;
+        const double du = __dadd_rn(__dadd_rn(aui, __dmul_rn(edge, bu1)),
+                                    i > 0 ? __dmul_rn(bu1, cu[i - 1]) : 0.0);
+        const double dv = __dadd_rn(__dadd_rn(avi, __dmul_rn(edge, bv1)),
+                                    i > 0 ? __dmul_rn(bv1, cv[i - 1]) : 0.0);
+        cu[i] = (i < n - 1) ? __ddiv_rn(-bu1, du) : 0.0;
+        cv[i] = (i < n - 1) ? __ddiv_rn(-bv1, dv) : 0.0;
+        ru[i] = __ddiv_rn(__dadd_rn(rU, i > 0 ? __dmul_rn(bu1, ru[i - 1]) : 0.0), du);
+        rv[i] = __ddiv_rn(__dadd_rn(rV, i > 0 ? __dmul_rn(bv1, rv[i - 1]) : 0.0), dv);
       }
       u[n - 1] = ru[n - 1];
       v[n - 1] = rv[n - 1];
       for (int i = n - 2; i >= 0; --i) {
-        u[i] = ru[i] - cu[i] * u[i + 1];
-        v[i] = rv[i] - cv[i] * v[i + 1];
+        u[i] = __dsub_rn(ru[i], __dmul_rn(cu[i], u[i + 1]));
+        v[i] = __dsub_rn(rv[i], __dmul_rn(cv[i], v[i + 1]));
       }
     } else {
-    if (grow) {  // rho_n = exp(r t_n): the matrix changes every step
-      const double rho = exp(r * (double)step * tau);
-      alpha = 1.0 + tau * 1.0 * r;  // m = 1 in 1-D
+    if (grow) {  // rho_n = rho(t_n): the matrix changes every step
+      double rho, q;
+      growth_at(pb, th, (double)step * tau, rho, q);
+      if (!(rho > 0.0)) {
+        bad = true;
+        break;
+      }
+      alpha = 1.0 + tau * 1.0 * q;  // m = 1 in 1-D
       bu = tau / (rho * rho) * h2inv;
       bv = tau * d / (rho * rho) * h2inv;
       thomas_factors<NMAX>(n, alpha, bu, cu, iu);
@@ -116,7 +156,35 @@ __device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
       v[i] = rv[i] - cv[i] * v[i + 1];
     }
     }
-    if (next_obs < S.n_obs && step + 1 == S.obs_steps[next_obs]) {
+    bool observe = !steady && next_obs < S.n_obs && step + 1 == S.obs_steps[next_obs];
+    if (steady) {
+      double s2 = 0.0;
+      for (int i = 0; i < n; ++i)
+        s2 += (u[i] - up[i]) * (u[i] - up[i]) + (v[i] - vp[i]) * (v[i] - vp[i]);
+      const double h = 1.0 / n;
+      if (phase == 0) {
+        if (sqrt(h * s2) / tau < pb.ss_tol) {
+          t_ss = step + 1;
+          observe = true;
+          if (!pb.ss_confirm) {
+            conv = true;
+          } else {
+            phase = 1;
+            for (int i = 0; i < n; ++i) {
+              up[i] = u[i];
+              vp[i] = v[i];
+            }
+          }
+        }
+      } else if (step + 1 == 2 * t_ss) {
+        conv = sqrt(h * s2) < pb.ss_tol;
+        for (int i = 0; i < n; ++i) {
+          u[i] = up[i];
+          v[i] = vp[i];
+        }
+      }
+    }
+    if (observe) {
       const double* yo = S.yd + (size_t)next_obs * nfo * n;
       int fo = 0;
       for (int f = 0; f < 2; ++f) {
@@ -131,9 +199,13 @@ __device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
       }
       ++next_obs;
     }
+    if (steady && ((phase == 0 && t_ss > 0) || (phase == 1 && step + 1 == 2 * t_ss))) break;
   }
-  *st_out = bad ? (uint32_t)RD_P_NONFINITE : 0u;
-  *phi_out = bad ? (double)INFINITY : phi * S.inv_two_sigma2;
+  const uint32_t st = (bad ? (uint32_t)RD_P_NONFINITE : 0u) |
+                      (conv ? 0u : (uint32_t)RD_P_NOT_CONVERGED);
+  *st_out = st;
+  *phi_out = st ? (double)INFINITY : phi * S.inv_two_sigma2;
+  if (steps_out) *steps_out = t_ss;
   if (fields_out) {
     for (int i = 0; i < n; ++i) {
       fields_out[i] = u[i];
@@ -145,15 +217,16 @@ __device__ void solve1d_item(const DevProblem& pb, const DevSize& S,
 template <int NMAX>
 __global__ void k_solve1d_f64(DevProblem pb, WorkQueue q, const double* theta,
                               double* phi, uint32_t* status, double* fields,
-                              size_t field_stride) {
+                              size_t field_stride, int* steps_out) {
   for (;;) {
     int s;
     const int b = queue_pop(q, &s);
     if (b < 0) break;
-    double th[5];
+    double th[kNPhys];
     full_theta(pb, theta + (size_t)b * pb.n_params, th);
     double* fo = fields ? fields + (size_t)b * field_stride : nullptr;
-    solve1d_item<NMAX>(pb, pb.sz[s], th, &phi[b], &status[b], fo);
+    solve1d_item<NMAX>(pb, pb.sz[s], th, &phi[b], &status[b], fo,
+                       steps_out ? &steps_out[b] : nullptr);
   }
 }
 
@@ -177,107 +250,19 @@ __global__ void k_solve1d_f64(DevProblem pb, WorkQueue q, const double* theta,
 // thread (ty, tx) owning rows ty + 16 i and columns tx + 16 j.  Rows are
 // padded to N + 1 floats so that every operand load is conflict-free.
 // ---------------------------------------------------------------------------
-constexpr int kSimtThreads = 256;
-
-template <int N>
-constexpr size_t simt_smem_bytes() {
-  return (size_t)3 * N * (N + 1) * sizeof(float);
-}
-
-// acc[i][j] = sum_k A(ty + 16 i, k) B(k, tx + 16 j), A(m, k) = pa[m*SAM + k*SAK],
-// B(k, n) = pb[k*SBK + n*SBN].
-template <int N, int SAM, int SAK, int SBK, int SBN>
-__device__ __forceinline__ void smem_gemm(const float* __restrict__ pa,
-                                          const float* __restrict__ pb,
-                                          float (&acc)[N / 16][N / 16], int ty,
-                                          int tx) {
-  constexpr int TM = N / 16;
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TM; ++j) acc[i][j] = 0.f;
-#pragma unroll 4
-  for (int k = 0; k < N; ++k) {
-    float av[TM], bv[TM];
-#pragma unroll
-    for (int i = 0; i < TM; ++i) av[i] = pa[(ty + 16 * i) * SAM + k * SAK];
-#pragma unroll
-    for (int j = 0; j < TM; ++j) bv[j] = pb[k * SBK + (tx + 16 * j) * SBN];
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-      for (int j = 0; j < TM; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-  }
-}
-
-template <int N>
-__device__ __forceinline__ void store_tile(float* W, const float (&acc)[N / 16][N / 16],
-                                           int ty, int tx) {
-  constexpr int TM = N / 16, NP = N + 1;
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TM; ++j) W[(ty + 16 * i) * NP + tx + 16 * j] = acc[i][j];
-}
-
-// In place: W <- [alpha I - beta Lap_h]^-1 W.
-template <int N>
-__device__ __forceinline__ void implicit_solve_simt(float* W, const float* Cm,
-                                                    float alpha, float beta,
-                                                    const float (&mur)[N / 16],
-                                                    const float (&muc)[N / 16],
-                                                    int ty, int tx) {
-  constexpr int TM = N / 16, NP = N + 1;
-  float acc[TM][TM];
-  // P[y][k] = sum_x W[y][x] C[k][x]
-  smem_gemm<N, NP, 1, 1, NP>(W, Cm, acc, ty, tx);
-  __syncthreads();
-  store_tile<N>(W, acc, ty, tx);
-  __syncthreads();
-  // Q[l][k] = sum_y C[l][y] P[y][k];  S = Q / (alpha + beta (mu_l + mu_k))
-  smem_gemm<N, NP, 1, NP, 1>(Cm, W, acc, ty, tx);
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TM; ++j) acc[i][j] *= tc::recip_nr(fmaf(beta, mur[i] + muc[j], alpha));
-  __syncthreads();
-  store_tile<N>(W, acc, ty, tx);
-  __syncthreads();
-  // W1[y][k] = sum_l C[l][y] S[l][k]
-  smem_gemm<N, 1, NP, NP, 1>(Cm, W, acc, ty, tx);
-  __syncthreads();
-  store_tile<N>(W, acc, ty, tx);
-  __syncthreads();
-  // W[y][x] = sum_k W1[y][k] C[k][x]
-  smem_gemm<N, NP, 1, NP, 1>(W, Cm, acc, ty, tx);
-  __syncthreads();
-  store_tile<N>(W, acc, ty, tx);
-  __syncthreads();
-}
-
-// FP64 sum over the CTA; result valid in thread 0.
-__device__ __forceinline__ double cta_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  __syncthreads();
-  return s;
-}
-
-template <int N>
+// STEADY: the steady-state mode of solve1d_item (rd_solve_simt.cu, above),
+// with the previous step (then w(T)) in two more shared-memory arrays.
+template <int N, bool STEADY>
 __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
-                                  const double th[5], float* sm, double* red,
+                                  const double th[kNPhys], float* sm, double* red,
                                   double* phi_out, uint32_t* st_out,
-                                  float* fields_out) {
+                                  float* fields_out, int* steps_out) {
   constexpr int TM = N / 16, NP = N + 1, NPTS = N * N;
   float* U = sm;  // u - ref_u
   float* V = sm + N * NP;  // v - ref_v
   float* Cm = sm + 2 * N * NP;
+  float* Up = sm + 3 * N * NP;  // STEADY only
+  float* Vp = sm + 4 * N * NP;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const float ref_u = S.ref_u, ref_v = S.ref_v;
   for (int i = tid; i < NPTS; i += kSimtThreads) {
@@ -300,8 +285,18 @@ __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
   double phi = 0.0;
   int bad = 0;
   int next_obs = 0;
+  int t_ss = 0, phase = 0;  // steady state: 0 seek T, 1 confirm to 2T
+  bool conv = !STEADY;
   __syncthreads();
-  for (int step = 0; step < pb.n_steps; ++step) {
+  for (int step = 0; STEADY || step < pb.n_steps; ++step) {
+    if (STEADY && phase == 0) {
+      if (step >= pb.n_steps) break;
+      for (int i = tid; i < NPTS; i += kSimtThreads) {  // the reaction pass below
+        const int o = (i / N) * NP + i % N;            // reads the same points
+        Up[o] = U[o];
+        Vp[o] = V[o];
+      }
+    }
     const double rho = exp(r * (double)step * tau);
     const double rho2inv = 1.0 / (rho * rho);
     const float alpha = (float)(1.0 + tau * 2.0 * r);  // m = 2 in 2-D
@@ -320,7 +315,44 @@ __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
     __syncthreads();
     implicit_solve_simt<N>(U, Cm, alpha, bu, mur, muc, ty, tx);
     implicit_solve_simt<N>(V, Cm, alpha, bv, mur, muc, ty, tx);
-    if (next_obs < S.n_obs && step + 1 == S.obs_steps[next_obs]) {
+    bool observe = !STEADY && next_obs < S.n_obs && step + 1 == S.obs_steps[next_obs];
+    bool stop = false;
+    if (STEADY) {
+      double part = 0.0;
+      for (int i = tid; i < NPTS; i += kSimtThreads) {
+        const int o = (i / N) * NP + i % N;
+        const double eu = (double)U[o] - (double)Up[o], ev = (double)V[o] - (double)Vp[o];
+        part += eu * eu + ev * ev;
+      }
+      const double h2 = 1.0 / ((double)N * N), s2 = cta_sum_all(part, red);
+      if (phase == 0) {
+        if (sqrt(h2 * s2) / tau < pb.ss_tol) {
+          t_ss = step + 1;
+          observe = true;
+          if (!pb.ss_confirm) {
+            conv = true;
+            stop = true;
+          } else {
+            phase = 1;
+            for (int i = tid; i < NPTS; i += kSimtThreads) {
+              const int o = (i / N) * NP + i % N;
+              Up[o] = U[o];
+              Vp[o] = V[o];
+            }
+          }
+        }
+      } else if (step + 1 == 2 * t_ss) {
+        conv = sqrt(h2 * s2) < pb.ss_tol;
+        stop = true;
+        for (int i = tid; i < NPTS; i += kSimtThreads) {
+          const int o = (i / N) * NP + i % N;
+          U[o] = Up[o];
+          V[o] = Vp[o];
+        }
+      }
+      __syncthreads();
+    }
+    if (observe) {
       const float* yo = S.yf + (size_t)next_obs * nfo * NPTS;
       int fo = 0;
       for (int f = 0; f < 2; ++f) {
@@ -339,12 +371,16 @@ __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
       }
       ++next_obs;
     }
+    if (stop) break;
   }
   const double tot = cta_sum(phi, red);
   const int any_bad = __syncthreads_or(bad);
   if (tid == 0) {
-    *st_out = any_bad ? (uint32_t)RD_P_NONFINITE : 0u;
-    *phi_out = any_bad ? (double)INFINITY : tot * S.inv_two_sigma2;
+    const uint32_t st = (any_bad ? (uint32_t)RD_P_NONFINITE : 0u) |
+                        (conv ? 0u : (uint32_t)RD_P_NOT_CONVERGED);
+    *st_out = st;
+    *phi_out = st ? (double)INFINITY : tot * S.inv_two_sigma2;
+    if (steps_out) *steps_out = t_ss;
   }
   if (fields_out) {
     for (int i = tid; i < NPTS; i += kSimtThreads) {
@@ -359,14 +395,15 @@ __device__ void solve2d_simt_item(const DevProblem& pb, const DevSize& S,
 #define RD_SIMT_CASE(NN)                                                      \
   case NN:                                                                    \
     if constexpr (NN <= NMAX)                                                 \
-      solve2d_simt_item<NN>(pb, S, th, sm, red, &phi[b], &status[b], fo);     \
+      solve2d_simt_item<NN, STEADY>(pb, S, th, sm, red, &phi[b], &status[b], fo, \
+                                    steps_out ? &steps_out[b] : nullptr);     \
     break;
 
 // NMAX: largest grid of the problem; sizes up to NMAX share one launch.
-template <int NMAX, int MINB>
+template <int NMAX, int MINB, bool STEADY>
 __global__ void __launch_bounds__(kSimtThreads, MINB)
     k_solve2d_simt(DevProblem pb, WorkQueue q, const double* theta, double* phi,
-                   uint32_t* status, float* fields, size_t field_stride) {
+                   uint32_t* status, float* fields, size_t field_stride, int* steps_out) {
   extern __shared__ __align__(16) float sm[];
   __shared__ double red[kSimtThreads / 32];
   __shared__ int s_item, s_size;
@@ -380,7 +417,7 @@ __global__ void __launch_bounds__(kSimtThreads, MINB)
     const int b = s_item, s = s_size;
     __syncthreads();
     if (b < 0) break;
-    double th[5];
+    double th[kNPhys];
     full_theta(pb, theta + (size_t)b * pb.n_params, th);
     const DevSize& S = pb.sz[s];
     float* fo = fields ? fields + (size_t)b * field_stride : nullptr;
@@ -400,8 +437,8 @@ __global__ void __launch_bounds__(kSimtThreads, MINB)
 }
 #undef RD_SIMT_CASE
 
-size_t simt2d_smem_bytes(int n) {
-  return (size_t)3 * n * (n + 1) * sizeof(float);
+size_t simt2d_smem_bytes(int n, bool steady) {
+  return (size_t)(steady ? 5 : 3) * n * (n + 1) * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,6 +454,9 @@ __global__ void k_fill_queue(WorkQueue q, int B, const int* size_idx,
     status[b] = RD_P_OUT_OF_SUPPORT;
     return;
   }
+  // pending until a solve kernel writes the result
+  phi[b] = (double)INFINITY;
+  status[b] = RD_P_NOT_SOLVED;
   const int i = atomicAdd(&q.counts[s], 1);
   q.items[(size_t)s * q.capacity + i] = b;
 }
@@ -431,48 +471,56 @@ cudaError_t launch_fill_queue(const WorkQueue& q, int B, const int* size_idx,
 
 // Kernel variant for a problem whose largest grid is max_n: the 1-D bucket
 // (local arrays of 64 or 256 doubles) or the 2-D NMAX instantiation with the
-// CTAs-per-SM hint that its shared memory allows.
+// CTAs-per-SM hint that its shared memory allows (steady-state mode: the
+// variant with the previous step's copy, N <= 96).
 template <typename F>
-static auto with_simt_kernel(int dim, int max_n, F&& f) {
+static auto with_simt_kernel(int dim, int max_n, bool steady, F&& f) {
   if (dim == 1) {
     if (max_n <= 64) return f((const void*)k_solve1d_f64<64>, 0);
     return f((const void*)k_solve1d_f64<256>, 0);
   }
-  if (max_n <= 32) return f((const void*)k_solve2d_simt<32, 4>, 32);
-  if (max_n <= 64) return f((const void*)k_solve2d_simt<64, 4>, 64);
-  if (max_n <= 96) return f((const void*)k_solve2d_simt<96, 2>, 96);
-  return f((const void*)k_solve2d_simt<128, 1>, 128);
+  if (steady) {
+    if (max_n <= 32) return f((const void*)k_solve2d_simt<32, 2, true>, 32);
+    if (max_n <= 64) return f((const void*)k_solve2d_simt<64, 2, true>, 64);
+    return f((const void*)k_solve2d_simt<96, 1, true>, 96);
+  }
+  if (max_n <= 32) return f((const void*)k_solve2d_simt<32, 4, false>, 32);
+  if (max_n <= 64) return f((const void*)k_solve2d_simt<64, 4, false>, 64);
+  if (max_n <= 96) return f((const void*)k_solve2d_simt<96, 2, false>, 96);
+  return f((const void*)k_solve2d_simt<128, 1, false>, 128);
 }
 
 cudaError_t launch_solve_simt(const DevProblem& pb, const WorkQueue& q,
                               const double* theta, double* phi, uint32_t* status,
-                              void* fields, int grid, cudaStream_t st) {
+                              void* fields, int grid, cudaStream_t st, int* steps_out) {
   const size_t stride = (size_t)2 * (pb.dim == 1 ? pb.max_n : pb.max_n * pb.max_n);
   const double* th = theta;
   void* fo = fields;
   DevProblem pbv = pb;
   WorkQueue qv = q;
   size_t stride_v = stride;
-  return with_simt_kernel(pb.dim, pb.max_n, [&](const void* fn, int nmax) {
-    const size_t smem = pb.dim == 1 ? 0 : simt2d_smem_bytes(nmax);
+  int* so = steps_out;
+  const bool steady = pb.ss_tol > 0.0;
+  return with_simt_kernel(pb.dim, pb.max_n, steady, [&](const void* fn, int nmax) {
+    const size_t smem = pb.dim == 1 ? 0 : simt2d_smem_bytes(nmax, steady);
     const int threads = pb.dim == 1 ? 128 : kSimtThreads;
-    void* args[] = {&pbv, &qv, (void*)&th, &phi, &status, &fo, &stride_v};
+    void* args[] = {&pbv, &qv, (void*)&th, &phi, &status, &fo, &stride_v, &so};
     return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st);
   });
 }
 
-cudaError_t setup_solve_simt(int dim, int max_n) {
-  return with_simt_kernel(dim, max_n, [&](const void* fn, int nmax) {
+cudaError_t setup_solve_simt(int dim, int max_n, bool steady) {
+  return with_simt_kernel(dim, max_n, steady, [&](const void* fn, int nmax) {
     if (dim == 1) return cudaSuccess;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)simt2d_smem_bytes(nmax));
+                                (int)simt2d_smem_bytes(nmax, steady));
   });
 }
 
-int grid_solve_simt(int dim, int max_n, int n_sm) {
-  return with_simt_kernel(dim, max_n, [&](const void* fn, int nmax) {
+int grid_solve_simt(int dim, int max_n, int n_sm, bool steady) {
+  return with_simt_kernel(dim, max_n, steady, [&](const void* fn, int nmax) {
     int per_sm = 0;
-    const size_t smem = dim == 1 ? 0 : simt2d_smem_bytes(nmax);
+    const size_t smem = dim == 1 ? 0 : simt2d_smem_bytes(nmax, steady);
     const int threads = dim == 1 ? 128 : kSimtThreads;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) !=
             cudaSuccess ||

@@ -53,6 +53,7 @@ struct TcCtrl {
   uint64_t rx_ready;      // both fields' stage-1 operands written (256)
   uint64_t st_ready;      // both converter groups past their stage-4 wait (256)
   uint64_t fin;           // drain of in-flight MMAs at exit
+  uint64_t never;         // completed by nothing (failure-path test aid)
   uint32_t tmem_base;
   int abort;
   int size;
@@ -60,7 +61,7 @@ struct TcCtrl {
   int items[kTcMaxStack];
   int bad[kTcMaxStack];
   double phi[kTcMaxStack];
-  double th[kTcMaxStack][5];
+  double th[kTcMaxStack][kNPhys];
   float mu[128];
 };
 
@@ -200,11 +201,11 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
   const float kap = tc_rz_comp(n);
   for (int step = 0;; ++step) {
     if (step > 0) {
-      if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
+      if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
       ++ph_done;
       tc_fence_after();
       mbar_arrive(&ctl->st_ready);
-      if (!mbar_wait_bounded(&ctl->st_ready, ph_st & 1u, abort)) return false;
+      if (!mbar_wait_bounded(&ctl->st_ready, ph_st & 1u, abort, pb.wait_ns)) return false;
       ++ph_st;
       tc_fence_after();
     }
@@ -282,7 +283,7 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     mbar_arrive(&ctl->rx_ready);
 
     // ---- stage 1 -> MN-major operand of stage 2 (row y, columns p n + k)
-    if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
+    if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
     ++ph_done;
     tc_fence_after();
     for (int k = 0; k < n; k += 8) {
@@ -300,7 +301,7 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     mbar_arrive(&ctl->op_ready[f]);
 
     // ---- stage 2 -> scale by L -> K-major operand of stage 3 (row l)
-    if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
+    if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
     ++ph_done;
     tc_fence_after();
     for (int c = 0; c < n; c += 8) {
@@ -329,7 +330,7 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     mbar_arrive(&ctl->op_ready[f]);
 
     // ---- stage 3 -> MN-major operand of stage 4 (row k, columns p n + y)
-    if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
+    if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
     ++ph_done;
     tc_fence_after();
     for (int y = 0; y < n; y += 8) {
@@ -360,7 +361,7 @@ __device__ bool tc_issuer(const DevProblem& pb, TcCtrl* ctl, uint8_t* base, int 
   volatile int* abort = &ctl->abort;
   const uint32_t d[2] = {tmem, tmem + (uint32_t)n};
   for (int step = 0; step < pb.n_steps; ++step) {
-    if (!mbar_wait_bounded(&ctl->rx_ready, ph_rx & 1u, abort)) return false;
+    if (!mbar_wait_bounded(&ctl->rx_ready, ph_rx & 1u, abort, pb.wait_ns)) return false;
     ++ph_rx;
     tc_fence_after();
     if (lane == 0) {
@@ -370,9 +371,13 @@ __device__ bool tc_issuer(const DevProblem& pb, TcCtrl* ctl, uint8_t* base, int 
       }
     }
     __syncwarp();
+    if (step == pb.stall_step) {  // test aid: wait on a barrier nothing completes
+      mbar_wait_bounded(&ctl->never, 0u, abort, pb.wait_ns);
+      return false;
+    }
     for (int stage = 2; stage <= 4; ++stage) {
       for (int f = 0; f < 2; ++f) {
-        if (!mbar_wait_bounded(&ctl->op_ready[f], ph_op[f] & 1u, abort)) return false;
+        if (!mbar_wait_bounded(&ctl->op_ready[f], ph_op[f] & 1u, abort, pb.wait_ns)) return false;
         ++ph_op[f];
         tc_fence_after();
         if (lane == 0) {
@@ -410,6 +415,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(&ctl->rx_ready, 256);
     mbar_init(&ctl->st_ready, 256);
     mbar_init(&ctl->fin, 1);
+    mbar_init(&ctl->never, 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }

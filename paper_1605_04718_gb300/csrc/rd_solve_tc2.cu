@@ -79,6 +79,7 @@ struct Ctrl {
   uint64_t rx_ready;      // reaction written (both fields)
   uint64_t st_ready;      // both fields' stage 4 observed
   uint64_t fin;
+  uint64_t never;         // completed by nothing (failure-path test aid)
   uint32_t tmem_base;
   int abort;
   int item;
@@ -260,11 +261,11 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
   int next_obs = 0;
   for (int step = 0;; ++step) {
     if (step > 0) {
-      if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
+      if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
       ++ph_done;
       tc_fence_after();
       mbar_arrive(&ctl->st_ready);
-      if (!mbar_wait_bounded(&ctl->st_ready, ph_st & 1u, abort)) return false;
+      if (!mbar_wait_bounded(&ctl->st_ready, ph_st & 1u, abort, pb.wait_ns)) return false;
       ++ph_st;
       tc_fence_after();
     }
@@ -314,21 +315,25 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
     // ---- stages 1-3 of field f -> operands of stages 2-4
 #pragma unroll 1
     for (int stage = 1; stage <= 3; ++stage) {
-      if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort)) return false;
+      if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
       ++ph_done;
       tc_fence_after();
       const float sc = stage == 1 ? kScale1 : stage == 3 ? kScale3 : 1.f;
       // this warp's 64 columns in 4 chunks of 16, the next chunk's TMEM load in
       // flight while the current one is converted
-      const int cols[4] = {CW * rr, CW * rr + 16, 64 + CW * rr, 64 + CW * rr + 16};
+      constexpr int NQ = CW / 8;  // chunks of 16 columns, both halves
+      int cols[NQ];
+#pragma unroll
+      for (int qq = 0; qq < NQ; ++qq)
+        cols[qq] = 64 * (qq / (NQ / 2)) + CW * rr + 16 * (qq % (NQ / 2));
       float buf[2][16];
       __syncwarp();
       tmem_ld16(t_f + (uint32_t)cols[0], buf[0]);
       tmem_wait_ld();
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < NQ; ++q) {
         float* a = buf[q & 1];
-        if (q < 3) tmem_ld16(t_f + (uint32_t)cols[q + 1], buf[(q + 1) & 1]);
+        if (q < NQ - 1) tmem_ld16(t_f + (uint32_t)cols[q + 1], buf[(q + 1) & 1]);
         const int c0 = cols[q];
         if (stage == 2) {  // S = D L, L from mu_l + mu_k two columns at a time
           const uint64_t ml2 = f2_pack(mu_l, mu_l), be2 = f2_pack(beta_f, beta_f);
@@ -348,7 +353,7 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
 #pragma unroll
           for (int k = 0; k < 16; k += 8) store8(hi_f, lo_f, l, c0 + k, a + k, sc);
         }
-        if (q < 3) tmem_wait_ld();
+        if (q < NQ - 1) tmem_wait_ld();
       }
       fence_proxy_async_smem();
       tc_fence_before();
@@ -364,7 +369,7 @@ __device__ bool issuer(const DevProblem& pb, Ctrl* ctl, uint8_t* base, uint32_t 
                        uint32_t& ph_rx, uint32_t (&ph_all)[2]) {
   volatile int* abort = &ctl->abort;
   for (int step = 0; step < pb.n_steps; ++step) {
-    if (!mbar_wait_bounded(&ctl->rx_ready, ph_rx & 1u, abort)) return false;
+    if (!mbar_wait_bounded(&ctl->rx_ready, ph_rx & 1u, abort, pb.wait_ns)) return false;
     ++ph_rx;
     tc_fence_after();
     if (lane == 0) {
@@ -375,11 +380,15 @@ __device__ bool issuer(const DevProblem& pb, Ctrl* ctl, uint8_t* base, uint32_t 
       }
     }
     __syncwarp();
+    if (step == pb.stall_step) {  // test aid: wait on a barrier nothing completes
+      mbar_wait_bounded(&ctl->never, 0u, abort, pb.wait_ns);
+      return false;
+    }
 #pragma unroll 1
     for (int stage = 2; stage <= 4; ++stage) {
 #pragma unroll
       for (int f = 0; f < 2; ++f) {
-        if (!mbar_wait_bounded(&ctl->op_all[f], ph_all[f] & 1u, abort)) return false;
+        if (!mbar_wait_bounded(&ctl->op_all[f], ph_all[f] & 1u, abort, pb.wait_ns)) return false;
         ++ph_all[f];
         tc_fence_after();
         if (lane == 0) {
@@ -423,6 +432,7 @@ __global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
     mbar_init(&ctl->rx_ready, 32 * kConvWarps);
     mbar_init(&ctl->st_ready, 32 * kConvWarps);
     mbar_init(&ctl->fin, 1);
+    mbar_init(&ctl->never, 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }

@@ -44,18 +44,23 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// Default limit of a bounded wait: 4 s of wall time.
+constexpr uint64_t kWaitLimitNs = 4000000000ull;
+
 // Bounded wait for the phase with the given parity.  Gives up (returns false)
-// when *abort is set by another thread, or after about 4 s of wall time (or
+// when *abort is set by another thread, or after limit_ns of wall time (or
 // 2^30 polls), in which case it sets *abort itself so that every other waiter
-// leaves too.  A healthy wait in these kernels lasts microseconds.
+// leaves too.  A healthy wait in these kernels lasts microseconds.  Every
+// lane of a warp polls with the same instruction, so a warp leaves as one.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  volatile int* abort) {
+                                                  volatile int* abort,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
     if ((it & 15u) == 15u &&
-        (globaltimer_ns() - t0 > 4000000000ull || it > (1u << 30))) {
+        (globaltimer_ns() - t0 > limit_ns || it > (1u << 30))) {
       *abort = 1;
       return false;
     }

@@ -19,11 +19,12 @@ def test_fastest_skips_missing_kernels():
 
 
 class _FakeLib:
-    """Stands in for the three C entry points tune() uses."""
+    """Stands in for the C entry points tune() uses."""
 
     def __init__(self, times):
         self.times = np.asarray(times, dtype=float)
         self.kernel = {}
+        self.ctas = {}
         self.calls = 0
 
     def autotune(self, p, theta, n_trials, probe_steps, n_sizes):
@@ -38,12 +39,20 @@ class _FakeLib:
     def get_kernel(self, p, s):
         return self.kernel[s]
 
+    def set_schedule(self, p, s, c):
+        self.ctas[s] = c
+
+    def get_schedule(self, p, s):
+        return 2 if self.kernel[s] == rd.RD_KERNEL_TC_STACKED else 1
+
 
 def test_tune_times_once_then_reuses_the_table(tmp_path, monkeypatch):
     fake = _FakeLib([[3e-3, 1e-3, math.nan], [9e-3, 4e-3, 2e-3]])
     monkeypatch.setattr(at, "rd_autotune", fake.autotune)
     monkeypatch.setattr(at, "rd_set_size_kernel", fake.set_kernel)
     monkeypatch.setattr(at, "rd_get_size_kernel", fake.get_kernel)
+    monkeypatch.setattr(at, "rd_set_size_schedule", fake.set_schedule)
+    monkeypatch.setattr(at, "rd_get_size_schedule", fake.get_schedule)
     path = str(tmp_path / "kernels.json")
     theta = np.zeros((8, 4))
     out = at.tune(None, "GPU-X", 2, [64, 128], 8000, theta, cache_path=path)
@@ -54,6 +63,7 @@ def test_tune_times_once_then_reuses_the_table(tmp_path, monkeypatch):
     again = at.tune(None, "GPU-X", 2, [64, 128], 8000, theta, cache_path=path)
     assert fake.calls == 1 and all(again[s]["cached"] for s in (0, 1))
     assert fake.kernel == {0: rd.RD_KERNEL_TC_STACKED, 1: rd.RD_KERNEL_TC_RESIDENT}
+    assert fake.ctas == {0: 2, 1: 1}  # the persisted schedules are applied too
     # another GPU, step count or size is a different key: timed again
     at.tune(None, "GPU-Y", 2, [64, 128], 8000, theta, cache_path=path)
     at.tune(None, "GPU-X", 2, [64, 96], 8000, theta, cache_path=path)

@@ -33,11 +33,13 @@ def test_autotune_times_and_choice():
     dss = [H.small_dataset(n, 40, seed=600 + n) for n in (32, 64, 128)]
     p = H.gpu_problem(dss, solver=rd.RD_SOLVER_AUTO)
     times = rd.rd_autotune(p, _draws(64, 1), n_trials=2, probe_steps=20, n_sizes=3)
-    assert times.shape == (3, 3)
+    assert times.shape == (3, 4)
+    assert np.all(np.isnan(times[:, 3]))  # CG needs every grid at N <= 96
     assert np.all(np.isfinite(times[:, :2])) and np.all(times[:, :2] > 0)
     assert np.isnan(times[0, 2]) and np.isnan(times[1, 2]) and np.isfinite(times[2, 2])
     for s in range(3):
         assert rd.rd_get_size_kernel(p, s) == at.fastest(times[s])
+        assert rd.rd_get_size_schedule(p, s) >= 1  # the searched CTAs-per-SM axis
     # the tuned kernels solve a mixed batch like the oracle
     B = 24
     theta = _draws(B, 2)

@@ -1,7 +1,9 @@
 """The paper's semi-implicit time step (Sec. 3.1.1, Example 1) on the GPU,
 through the C ABI, against the FP64 oracle: 1-D fields and Phi on a fixed and
 on a growing domain, chains with the same random streams, and the argument
-checks."""
+checks; in 2-D (preconditioned CG on the CUDA cores) fields and Phi on two
+grid sizes, the paper's gamma = 1000 setting and its fixed steady state; and
+the plain-CG IMEX kernel (RD_KERNEL_CG) against the oracle."""
 import numpy as np
 import pytest
 import torch
@@ -85,8 +87,121 @@ def test_picard_chains_match_oracle_and_argument_checks():
     with pytest.raises(rd.RdError):
         rd.rd_set_scheme(p, 7)
     rd.rd_problem_destroy(p)
-    ds2 = H.small_dataset(32, 4, seed=3)
+    ds2 = H.small_dataset(96, 4, seed=3)
     p2 = H.gpu_problem([ds2])
     with pytest.raises(rd.RdError):
-        rd.rd_set_scheme(p2, rd.RD_SCHEME_PICARD)  # 2-D: not built
+        rd.rd_set_scheme(p2, rd.RD_SCHEME_PICARD)  # 2-D: grids up to 80 only
     rd.rd_problem_destroy(p2)
+
+
+# ---- 2-D: preconditioned CG on the CUDA cores ------------------------------
+
+def _picard2d(dss, theta, fixed=None):
+    """GPU and oracle results of the semi-implicit step for proposals theta
+    (natural units, [B][4]) on the 2-D datasets dss (size i % len(dss))."""
+    p = H.gpu_problem(dss, solver=rd.RD_SOLVER_AUTO, fixed=fixed)
+    rd.rd_set_scheme(p, rd.RD_SCHEME_PICARD)
+    B = theta.shape[0]
+    nmax = max(d["n"] for d in dss)
+    th = torch.tensor(theta, dtype=torch.float64, device=DEV)
+    sz = torch.tensor(np.arange(B) % len(dss), dtype=torch.int32, device=DEV)
+    phi = torch.zeros(B, dtype=torch.float64, device=DEV)
+    st = torch.zeros(B, dtype=torch.int32, device=DEV)
+    fl = torch.full((B, 2, nmax, nmax), float("nan"), dtype=torch.float32, device=DEV)
+    rd.rd_evaluate_batch(p, th, phi, st, size_idx=sz, fields=fl)
+    rd.rd_sync(p)
+    rd.rd_problem_destroy(p)
+    return phi.cpu().numpy(), st.cpu().numpy(), fl.double().cpu().numpy()
+
+
+def _oracle2d(ds, theta):
+    P = oracle.Problem(2, ds["n"], ds["tau"], ds["n_steps"], ds["u0"], ds["v0"], y=ds["y"],
+                       obs_steps=ds["obs_steps"], field_mask=ds["field_mask"],
+                       sigma=ds["sigma"], scheme="picard")
+    th5 = np.concatenate([theta, np.zeros((len(theta), 1))], 1)
+    return P.forward_batch(th5, want_fields=True)
+
+
+def test_picard_2d_fields_and_phi_match_oracle():
+    """Two grid sizes in one launch, prior draws around the truth, 200
+    steps: fields within relative L2 1e-3 (FP32) of the FP64 oracle's CG
+    solution, Phi within what that allows."""
+    dss = [H.small_dataset(n, 200, seed=60 + n) for n in (32, 64)]
+    B = 24
+    theta = rd_synth.lognormal_draws([0.1, 0.9, 10.0, 200.0], [0.15] * 4, B, seed=17)
+    phi, st, fl = _picard2d(dss, theta)
+    for s, ds in enumerate(dss):
+        n = ds["n"]
+        rows = np.arange(B)[np.arange(B) % 2 == s]
+        po, so, fo = _oracle2d(ds, theta[rows])
+        for k, i in enumerate(rows):
+            assert st[i] == so[k]
+            if so[k]:
+                continue
+            w_g = fl[i].reshape(-1)[: 2 * n * n].reshape(2, -1)
+            w_o = fo[k].reshape(2, -1)
+            assert H.rel_l2(w_g, w_o) < 1e-3, (i, H.rel_l2(w_g, w_o))
+            tol = H.phi_tolerance(ds["y"].reshape(-1), w_o.reshape(-1), ds["sigma"])
+            assert abs(phi[i] - po[k]) <= tol, (i, phi[i], po[k], tol)
+
+
+def test_picard_2d_paper_parameters_and_steady_state():
+    """The paper's Example-2 setting (gamma = 1000, tau = 1e-4, Table 1's a,
+    b): a pattern grows from the perturbed steady state in step with the
+    oracle; from the exact homogeneous steady state nothing moves."""
+    a, b = 0.126779, 0.792366
+    us, vs = oracle.steady_state(a, b)
+    n = 64
+    ds = H.small_dataset(n, 400, tau=1e-4, seed=71)
+    ds = dict(ds, u0=ds["u0"] - 1.0 + us, v0=ds["v0"] - 0.9 + vs)  # (a, b)'s steady state
+    flat = dict(ds, u0=np.full((n, n), us), v0=np.full((n, n), vs))
+    theta = np.array([[a, b, 10.0, 1000.0]])
+    for d_ in (ds, flat):
+        phi, st, fl = _picard2d([d_], theta)
+        po, so, fo = _oracle2d(d_, theta)
+        assert st[0] == so[0] == 0
+        w_g = fl[0].reshape(2, -1)
+        assert H.rel_l2(w_g, fo[0].reshape(2, -1)) < 1e-3
+        if d_ is flat:
+            assert np.max(np.abs(w_g[0] - us)) < 1e-5 and np.max(np.abs(w_g[1] - vs)) < 1e-5
+
+
+def test_cg_kernel_matches_oracle():
+    """RD_KERNEL_CG (the IMEX step with each implicit system solved by plain
+    CG) on 32^2, 64^2 and 96^2 in one launch, against the oracle's eigenbasis
+    solve: fields within relative L2 1e-3, Phi within what that allows."""
+    dss = [H.small_dataset(n, 100, seed=80 + n) for n in (32, 64, 96)]
+    p = H.gpu_problem(dss, solver=rd.RD_SOLVER_AUTO)
+    for s in range(3):
+        rd.rd_set_size_kernel(p, s, rd.RD_KERNEL_CG)
+    assert rd.rd_get_size_kernel(p, 2) == rd.RD_KERNEL_CG
+    B = 18
+    theta = rd_synth.lognormal_draws([0.1, 0.9, 10.0, 200.0], [0.15] * 4, B, seed=19)
+    th = torch.tensor(theta, dtype=torch.float64, device=DEV)
+    sz = torch.tensor(np.arange(B) % 3, dtype=torch.int32, device=DEV)
+    phi = torch.zeros(B, dtype=torch.float64, device=DEV)
+    st = torch.zeros(B, dtype=torch.int32, device=DEV)
+    fl = torch.full((B, 2, 96, 96), float("nan"), dtype=torch.float32, device=DEV)
+    rd.rd_evaluate_batch(p, th, phi, st, size_idx=sz, fields=fl)
+    rd.rd_sync(p)
+    phi, st, fl = phi.cpu().numpy(), st.cpu().numpy(), fl.double().cpu().numpy()
+    for s, ds in enumerate(dss):
+        n = ds["n"]
+        P = H.oracle_problem(ds)
+        for i in np.arange(B)[np.arange(B) % 3 == s]:
+            po, so, uo, vo = P.forward(list(theta[i]) + [0.0])
+            assert st[i] == so
+            if so:
+                continue
+            w_g = fl[i].reshape(-1)[: 2 * n * n].reshape(2, -1)
+            w_o = np.stack([uo, vo]).reshape(2, -1)
+            assert H.rel_l2(w_g, w_o) < 1e-3, (i, H.rel_l2(w_g, w_o))
+            tol = H.phi_tolerance(ds["y"].reshape(-1), w_o.reshape(-1), ds["sigma"])
+            assert abs(phi[i] - po) <= tol
+    with pytest.raises(rd.RdError):  # a 128^2 grid is beyond its shared memory
+        p2 = H.gpu_problem([H.small_dataset(128, 4, seed=2)], solver=rd.RD_SOLVER_AUTO)
+        try:
+            rd.rd_set_size_kernel(p2, 0, rd.RD_KERNEL_CG)
+        finally:
+            rd.rd_problem_destroy(p2)
+    rd.rd_problem_destroy(p)
