@@ -28,16 +28,19 @@ namespace rd {
 static __device__ __align__(256) int
     g_noalloc_queue[RD_MAX_SIZES * RD_NOALLOC_MAX_BATCH + 2 * RD_MAX_SIZES];
 
-// Device address of g_noalloc_queue on each device, looked up once per device
-// (in host code the symbol is only a host-side stand-in, never an address the
-// GPU can use).
+// Device address of g_noalloc_queue on each device (in host code the symbol
+// is only a host-side stand-in, never an address the GPU can use).  Looked up
+// by rd_problem_create, once per device with that device current: the lookup
+// loads this file's module, and with it the array, onto the device, so it
+// belongs in a call that allocates anyway; rd_evaluate_batch_noalloc then
+// only reads the cached address.
 constexpr int kMaxDevices = 64;
 static int* g_noalloc_addr[kMaxDevices] = {};
 static std::mutex g_noalloc_mutex;
 
-static rd_status noalloc_scratch(int device, int** out) {
+rd_status noalloc_prepare(int device) {
   if (device < 0 || device >= kMaxDevices) {
-    set_error("rd_evaluate_batch_noalloc: device index out of range");
+    set_error("device index out of range for the allocation-free scratch");
     return RD_EINVAL;
   }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -45,14 +48,19 @@ static rd_status noalloc_scratch(int device, int** out) {
     void* ptr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_queue);
     if (e != cudaSuccess || !ptr) {
-      set_error(std::string("rd_evaluate_batch_noalloc: cudaGetSymbolAddress failed: ") +
+      set_error(std::string("cudaGetSymbolAddress of the allocation-free scratch failed: ") +
                 cudaGetErrorString(e));
       return RD_ECUDA;
     }
     g_noalloc_addr[device] = static_cast<int*>(ptr);
   }
-  *out = g_noalloc_addr[device];
   return RD_OK;
+}
+
+static int* noalloc_scratch(int device) {
+  if (device < 0 || device >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  return g_noalloc_addr[device];
 }
 
 }  // namespace rd
@@ -88,9 +96,11 @@ extern "C" rd_status rd_evaluate_batch_noalloc(rd_problem* p, int B, const doubl
     set_error("rd_evaluate_batch_noalloc: the problem's device must be the current device");
     return RD_EINVAL;
   }
-  int* scratch = nullptr;
-  const rd_status rs = noalloc_scratch(device, &scratch);
-  if (rs != RD_OK) return rs;
+  int* scratch = noalloc_scratch(device);  // looked up by rd_problem_create
+  if (!scratch) {
+    set_error("rd_evaluate_batch_noalloc: scratch address not prepared for this device");
+    return RD_ESTATE;
+  }
   WorkQueue q = make_queue(p);  // sizes and their order; storage replaced below
   q.items = scratch;
   q.capacity = RD_NOALLOC_MAX_BATCH;

@@ -3,7 +3,9 @@ allocate device memory during a call (their device memory is reserved by
 another allocator, or they must not stall on cudaFree's synchronisation):
 through the C ABI it must give the same results as rd_evaluate_batch, twice
 in a row (its fixed scratch keeps the previous call's contents), leave the
-device's free memory unchanged, and reject batches beyond its fixed limit.
+device's free memory unchanged from before its first call on a new problem
+even for a batch that rd_evaluate_batch would have to grow its workspace
+for, and reject batches beyond its fixed limit.
 This file is collected last so that a failure here comes after every other
 test has run."""
 import ctypes
@@ -38,39 +40,53 @@ def _buffers(B, n):
 @pytest.mark.parametrize("solver", [rd.RD_SOLVER_DCT_TC, rd.RD_SOLVER_DCT_SIMT])
 def test_noalloc_matches_evaluate_batch_twice(solver):
     dss = [H.small_dataset(n, 60, seed=500 + n) for n in (32, 64)]
-    p = H.gpu_problem(dss, solver=solver)
-    B = 50
+    dev = torch.device("cuda:0")
+    # a batch larger than a new problem's workspace (1024 work-list slots), so
+    # that rd_evaluate_batch would have to grow it with cudaMalloc
+    B = 4096
     theta = rd_synth.lognormal_draws([0.1, 0.9, 10.0, 200.0], [0.15] * 4, B, seed=21)
     theta[3, 3] = 5e4  # one divergent proposal: NONFINITE on both paths
-    dev = torch.device("cuda:0")
     th = torch.tensor(theta, dtype=torch.float64, device=dev)
     sz = torch.tensor(np.arange(B) % 2, dtype=torch.int32, device=dev)
+    # load the solve kernels once on another problem, so that the driver's
+    # loading of code on first launch is not counted below
+    warm = H.gpu_problem(dss, solver=solver)
+    pw, sw, fw = _buffers(B, 64)
+    rd.rd_evaluate_batch(warm, th, pw, sw, size_idx=sz, fields=fw)
+    rd.rd_sync(warm)
+    rd.rd_problem_destroy(warm)
+    del pw, sw, fw
+    p = H.gpu_problem(dss, solver=solver)  # fresh problem: no call has run on it
+    # output buffers of both calls allocated and filled beforehand: nothing but
+    # the calls themselves runs between the free-memory readings
+    bufs = [_buffers(B, 64) for _ in range(2)]
+    results = []
+    torch.cuda.synchronize(dev)
+    free_before = torch.cuda.mem_get_info(dev)[0]
+    for phi1, st1, fl1 in bufs:
+        rd.rd_evaluate_batch_noalloc(p, th, phi1, st1, size_idx=sz, fields=fl1)
+        rd.rd_sync(p)
+        assert torch.cuda.mem_get_info(dev)[0] == free_before  # the call allocated nothing
+    for phi1, st1, fl1 in bufs:
+        results.append((phi1.cpu().numpy(), st1.cpu().numpy(), fl1.double().cpu().numpy()))
+    # the existing entry point afterwards (it grows the workspace) as the reference
     phi0, st0, fl0 = _buffers(B, 64)
     rd.rd_evaluate_batch(p, th, phi0, st0, size_idx=sz, fields=fl0)
     rd.rd_sync(p)
-    free_after = []
-    phi1, st1, fl1 = _buffers(B, 64)  # allocated once: torch must not allocate in the loop
-    for _ in range(2):
-        phi1.fill_(0.0)
-        st1.fill_(0)
-        fl1.fill_(float("nan"))
-        rd.rd_evaluate_batch_noalloc(p, th, phi1, st1, size_idx=sz, fields=fl1)
-        rd.rd_sync(p)
-        free_after.append(torch.cuda.mem_get_info(dev)[0])
-        s0, s1 = st0.cpu().numpy(), st1.cpu().numpy()
+    p0, s0, f0 = phi0.cpu().numpy(), st0.cpu().numpy(), fl0.double().cpu().numpy()
+    for p1, s1, f1 in results:
         assert np.array_equal(s0, s1)
         assert s1[3] & rd.RD_P_NONFINITE
         ok = s0 == 0
-        p0, p1 = phi0.cpu().numpy(), phi1.cpu().numpy()
+        assert ok.sum() > B // 2
         assert np.all(np.abs(p1[ok] - p0[ok]) <= 1e-6 * np.abs(p0[ok]))
         assert np.all(np.isinf(p1[~ok]))
-        f0, f1 = fl0.double().cpu().numpy(), fl1.double().cpu().numpy()
-        for i in np.nonzero(ok)[0]:
-            n = 32 if i % 2 == 0 else 64
-            a = f0[i].reshape(-1)[: 2 * n * n]
-            b = f1[i].reshape(-1)[: 2 * n * n]
-            assert H.rel_l2(b, a) < 1e-6
-    assert free_after[0] == free_after[1]  # the second call allocated nothing
+        for parity, n in ((0, 32), (1, 64)):
+            idx = np.nonzero(ok & (np.arange(B) % 2 == parity))[0]
+            a = f0[idx].reshape(len(idx), -1)[:, : 2 * n * n]
+            b = f1[idx].reshape(len(idx), -1)[:, : 2 * n * n]
+            err = np.sqrt(((b - a) ** 2).sum(1) / (a ** 2).sum(1))
+            assert err.max() < 1e-6
     rd.rd_problem_destroy(p)
 
 
