@@ -86,7 +86,7 @@ struct Ctrl {
   int size;
   int bad;
   double phi;
-  double th[5];
+  double th[kNPhys];
   float mu[N];
 };
 

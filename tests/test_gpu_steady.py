@@ -101,10 +101,16 @@ def test_steady_state_2d_matches_the_oracle_protocol():
     p, (phi, st, steps, fl) = _gpu(2, n, tau, 300000, u0, v0, y.reshape(2, n, n), sigma,
                                    theta, thr)
     assert st[0] == 0
-    assert abs(int(steps[0]) - ref["steps_T"]) <= 0.1 * ref["steps_T"], (steps[0], ref)
-    w_o = np.stack([ref["u"], ref["v"]]).reshape(2, -1)
+    T = int(steps[0])
+    assert abs(T - ref["steps_T"]) <= 0.1 * ref["steps_T"], (T, ref["steps_T"])
+    # the state the GPU stopped in against the oracle's state at the same step
+    # (the approach to the steady state is slow, so states a few hundred steps
+    # apart differ by more than the FP32 tolerance)
+    P = oracle.Problem(2, n, tau, T, u0, v0, y=y.reshape(1, 2, n, n), obs_steps=[T],
+                       field_mask=3, sigma=sigma)
+    phi_o, _, uo, vo = P.forward([A, B_, 10.0, 200.0, 0.0])
+    w_o = np.stack([uo, vo]).reshape(2, -1)
     assert H.rel_l2(fl[0].reshape(2, -1), w_o) < 1e-3
-    phi_o = ((y.reshape(2, -1) - w_o) ** 2).sum() / (2 * sigma**2)
     assert abs(phi[0] - phi_o) <= H.phi_tolerance(y.reshape(-1), w_o.reshape(-1), sigma)
     with pytest.raises(rd.RdError):  # 128^2 is beyond the CUDA-core kernel's copy
         d128 = H.small_dataset(128, 4, seed=1)
