@@ -88,17 +88,53 @@ __host__ __device__ constexpr uint32_t tc_tmem_cols(int nmax) {
   return 4 * nmax <= 32 ? 32 : 4 * nmax <= 64 ? 64 : 4 * nmax <= 128 ? 128 : 4 * nmax <= 256 ? 256 : 512;
 }
 
-// Stores 8 consecutive columns c..c+7 (c % 8 == 0) of row r as FP16 hi and
-// lo parts into a swizzled tile pair.
+// Stores 8 consecutive columns c..c+7 (c % 8 == 0) of row r, each times
+// scale, as FP16 hi and lo parts into a swizzled tile pair (the split on
+// pairs of values with the paired FP32 instructions).
 __device__ __forceinline__ void store_split8(uint8_t* hi_tile, uint8_t* lo_tile, int rows,
-                                             int r, int c, const float (&x)[8]) {
-  __align__(16) __half h[8];
-  __align__(16) __half l[8];
+                                             int r, int c, const float* x, float scale) {
+  uint32_t h[4], l[4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) split_f16(x[j], h[j], l[j]);
+  for (int j = 0; j < 4; ++j) split_f16x2_scaled(x[2 * j], x[2 * j + 1], scale, h[j], l[j]);
   const uint32_t off = sw128_offset(rows, r, c);
-  *reinterpret_cast<uint4*>(hi_tile + off) = *reinterpret_cast<const uint4*>(h);
-  *reinterpret_cast<uint4*>(lo_tile + off) = *reinterpret_cast<const uint4*>(l);
+  *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// As store_split8 with one scale per value.
+__device__ __forceinline__ void store_split8v(uint8_t* hi_tile, uint8_t* lo_tile, int rows,
+                                              int r, int c, const float* x, const float* s8) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    split_f16x2_scaled2(x[2 * j], x[2 * j + 1], s8[2 * j], s8[2 * j + 1], h[j], l[j]);
+  const uint32_t off = sw128_offset(rows, r, c);
+  *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Runs fn(c, v) over this lane's n accumulator columns at t_acc in chunks of
+// 16 (v = the chunk's values), the next chunk's TMEM load in flight while
+// the current one is converted.  n is a multiple of 16 and warp-uniform.
+template <class F>
+__device__ __forceinline__ void convert_cols(uint32_t t_acc, int n, F&& fn) {
+  float b0[16], b1[16];
+  const int nq = n / 16;
+  __syncwarp();
+  tmem_ld16(t_acc, b0);
+  tmem_wait_ld();
+#pragma unroll 1
+  for (int q = 0; q < nq; q += 2) {
+    const bool has1 = q + 1 < nq, has2 = q + 2 < nq;
+    if (has1) tmem_ld16(t_acc + (uint32_t)(16 * (q + 1)), b1);
+    fn(16 * q, b0);
+    if (has1) {
+      tmem_wait_ld();
+      if (has2) tmem_ld16(t_acc + (uint32_t)(16 * (q + 2)), b0);
+      fn(16 * (q + 1), b1);
+      if (has2) tmem_wait_ld();
+    }
+  }
 }
 
 __device__ __forceinline__ void store_zero8(uint8_t* hi_tile, uint8_t* lo_tile, int rows, int r,
@@ -270,11 +306,11 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
       for (int j = 0; j < 8; ++j) {
         const float uu = ref_u + du[j], vv = ref_v + dv[j];
         const float u2v = uu * uu * vv;
-        ru[j] = (fmaf(ftg, fa - uu + u2v, du[j]) + cu) * 256.f;
-        rv[j] = (fmaf(ftg, fb - u2v, dv[j]) + cv) * 256.f;
+        ru[j] = fmaf(ftg, fa - uu + u2v, du[j]) + cu;
+        rv[j] = fmaf(ftg, fb - u2v, dv[j]) + cv;
       }
-      store_split8(op_hi[0], op_lo[0], 128, l, x, ru);
-      store_split8(op_hi[1], op_lo[1], 128, l, x, rv);
+      store_split8(op_hi[0], op_lo[0], 128, l, x, ru, 256.f);
+      store_split8(op_hi[1], op_lo[1], 128, l, x, rv, 256.f);
     }
     if (obs) ++next_obs;
     if (last) break;
@@ -286,15 +322,13 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
     ++ph_done;
     tc_fence_after();
-    for (int k = 0; k < n; k += 8) {
-      float a8[8];
-      __syncwarp();
-      tmem_ld8(t_acc_f + (uint32_t)k, a8);
-      tmem_wait_ld();
-      if (!lane_used) continue;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) a8[j] = fmaf(a8[j] * (1.f / 128.f), kap, a8[j] * (1.f / 128.f));
-      store_split8(op_hi[f], op_lo[f], n, row, p * n + k, a8);
+    {
+      const float sc1 = (1.f / 128.f) * (1.f + kap);
+      convert_cols(t_acc_f, n, [&](int k, const float* v) {
+        if (!lane_used) return;
+        store_split8(op_hi[f], op_lo[f], n, row, p * n + k, v, sc1);
+        store_split8(op_hi[f], op_lo[f], n, row, p * n + k + 8, v + 8, sc1);
+      });
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -304,26 +338,35 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
     ++ph_done;
     tc_fence_after();
-    for (int c = 0; c < n; c += 8) {
-      float a8[8], l8[8];
-      __syncwarp();
-      tmem_ld8(t_acc_f + (uint32_t)c, a8);
-      if (!pb.growth) tmem_ld8(t_lam + (uint32_t)c, l8);
-      tmem_wait_ld();
-      if (!lane_used) {
-        store_zero8(op_hi[f], op_lo[f], 128, l, c);
-        continue;
-      }
-      if (pb.growth) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          l8[j] = (1.f / 64.f) * recip_nr(fmaf(beta_f, ctl->mu[c + j] + mu_row, alpha));
-          l8[j] = fmaf(l8[j], kap, l8[j]);
+    if (!pb.growth) {  // L from its TMEM table, loaded with the accumulator
+      for (int c = 0; c < n; c += 8) {
+        float a8[8], l8[8];
+        __syncwarp();
+        tmem_ld8(t_acc_f + (uint32_t)c, a8);
+        tmem_ld8(t_lam + (uint32_t)c, l8);
+        tmem_wait_ld();
+        if (!lane_used) {
+          store_zero8(op_hi[f], op_lo[f], 128, l, c);
+          continue;
         }
+        store_split8v(op_hi[f], op_lo[f], 128, l, c, a8, l8);
       }
+    } else {
+      convert_cols(t_acc_f, n, [&](int c, const float* v) {
+        if (!lane_used) {
+          store_zero8(op_hi[f], op_lo[f], 128, l, c);
+          store_zero8(op_hi[f], op_lo[f], 128, l, c + 8);
+          return;
+        }
+        float l16[16];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a8[j] *= l8[j];
-      store_split8(op_hi[f], op_lo[f], 128, l, c, a8);
+        for (int j = 0; j < 16; ++j) {
+          l16[j] = (1.f / 64.f) * recip_nr(fmaf(beta_f, ctl->mu[c + j] + mu_row, alpha));
+          l16[j] = fmaf(l16[j], kap, l16[j]);
+        }
+        store_split8v(op_hi[f], op_lo[f], 128, l, c, v, l16);
+        store_split8v(op_hi[f], op_lo[f], 128, l, c + 8, v + 8, l16 + 8);
+      });
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -333,15 +376,13 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
     ++ph_done;
     tc_fence_after();
-    for (int y = 0; y < n; y += 8) {
-      float a8[8];
-      __syncwarp();
-      tmem_ld8(t_acc_f + (uint32_t)y, a8);
-      tmem_wait_ld();
-      if (!lane_used) continue;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) a8[j] = fmaf(a8[j], kap, a8[j]);
-      store_split8(op_hi[f], op_lo[f], n, row, p * n + y, a8);
+    {
+      const float sc3 = 1.f + kap;
+      convert_cols(t_acc_f, n, [&](int y, const float* v) {
+        if (!lane_used) return;
+        store_split8(op_hi[f], op_lo[f], n, row, p * n + y, v, sc3);
+        store_split8(op_hi[f], op_lo[f], n, row, p * n + y + 8, v + 8, sc3);
+      });
     }
     fence_proxy_async_smem();
     tc_fence_before();

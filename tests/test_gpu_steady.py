@@ -55,9 +55,17 @@ def _oracle(dim, n, tau, theta, u0, v0, threshold):
 
 
 def _data(dim, n, tau, threshold, seed):
-    u0, v0 = protocol.paper_initial_state(dim, n, A, B_)
-    if dim == 2:  # the GPU stores 2-D states in FP32: both sides read those values
-        u0, v0 = u0.astype(np.float32).astype(np.float64), v0.astype(np.float32).astype(np.float64)
+    if dim == 1:
+        u0, v0 = protocol.paper_initial_state(dim, n, A, B_)
+    else:
+        # eq. (ic_numerical) is symmetric under (x, y) -> (1 - x, 1 - y) and its
+        # symmetric pattern drifts slowly once rounding breaks the symmetry
+        # (FP32 breaks it sooner than FP64); seeded noise on the homogeneous
+        # steady state gives a generic pattern, stored in FP32 as the GPU does
+        us, vs = oracle.steady_state(A, B_)
+        noise = rd_synth.uniform_noise((2, n, n), seed, 0.01)
+        u0 = (us + noise[0]).astype(np.float32).astype(np.float64)
+        v0 = (vs + noise[1]).astype(np.float32).astype(np.float64)
     ref = _oracle(dim, n, tau, [A, B_], u0, v0, threshold)
     rng = np.random.default_rng(seed)
     yu, sigma = protocol.range_noise(ref["u"], 0.05, rng)
