@@ -17,7 +17,9 @@
 //
 // Precision: each FP32 operand x is split into FP16 hi + lo and each product
 // is formed as hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32
-// resolution), giving about 22 significant bits per element.  The small
+// resolution), giving about 22 significant bits per element.  The data's lo
+// part is stored negated (one instruction less per pair in the split) and
+// the MMAs that read it negate it back (descriptor bit).  The small
 // hi*lo and lo*hi products are issued before the hi*hi ones and each stage's
 // output is scaled by 1 + n 2^-29 against the tensor core's round-toward-zero
 // accumulation (tc_rz_comp).  Power-of-two
@@ -30,8 +32,10 @@
 //
 // Warp roles (288 threads): warps 0-3 convert field u, warps 4-7 field v
 // (warp w reads TMEM lanes 32 (w % 4) ...), warp 8 allocates TMEM and issues
-// the MMAs.  Hand-offs use mbarriers; every wait is bounded and a timed-out
-// wait makes the whole CTA leave, free its TMEM and raise the error flag.
+// the MMAs, one thread, in the order u1 v1 u2 v2 ... u4 v4, so that they
+// also complete in that order.  Hand-offs use mbarriers (one arrival per
+// warp); every wait is bounded and a timed-out wait makes the whole CTA
+// leave, free its TMEM and raise the error flag.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -49,9 +53,8 @@ constexpr int kTcMaxStack = 8;  // proposals per CTA (128 / 16)
 
 struct TcCtrl {
   uint64_t mma_done[2];   // stage MMAs of field f completed (tcgen05.commit)
-  uint64_t op_ready[2];   // operand of the next stage of field f written (128)
-  uint64_t rx_ready;      // both fields' stage-1 operands written (256)
-  uint64_t st_ready;      // both converter groups past their stage-4 wait (256)
+  uint64_t op_ready[2];   // operand of the next stage of field f written (4 warps)
+  uint64_t rx_ready;      // both fields' stage-1 operands written (8 warps)
   uint64_t fin;           // drain of in-flight MMAs at exit
   uint64_t never;         // completed by nothing (failure-path test aid)
   uint32_t tmem_base;
@@ -89,13 +92,24 @@ __host__ __device__ constexpr uint32_t tc_tmem_cols(int nmax) {
 }
 
 // Stores 8 consecutive columns c..c+7 (c % 8 == 0) of row r, each times
-// scale, as FP16 hi and lo parts into a swizzled tile pair (the split on
-// pairs of values with the paired FP32 instructions).
+// scale, as FP16 hi and negated lo parts into a swizzled tile pair (the
+// split on pairs of values with the paired FP32 instructions).
 __device__ __forceinline__ void store_split8(uint8_t* hi_tile, uint8_t* lo_tile, int rows,
                                              int r, int c, const float* x, float scale) {
   uint32_t h[4], l[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) split_f16x2_scaled(x[2 * j], x[2 * j + 1], scale, h[j], l[j]);
+  for (int j = 0; j < 4; ++j) split_f16x2_neglo_scaled(x[2 * j], x[2 * j + 1], scale, h[j], l[j]);
+  const uint32_t off = sw128_offset(rows, r, c);
+  *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// As store_split8 without a scale.
+__device__ __forceinline__ void store_split8n(uint8_t* hi_tile, uint8_t* lo_tile, int rows,
+                                              int r, int c, const float* x) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) split_f16x2_neglo(x[2 * j], x[2 * j + 1], h[j], l[j]);
   const uint32_t off = sw128_offset(rows, r, c);
   *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
@@ -107,7 +121,7 @@ __device__ __forceinline__ void store_split8v(uint8_t* hi_tile, uint8_t* lo_tile
   uint32_t h[4], l[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j)
-    split_f16x2_scaled2(x[2 * j], x[2 * j + 1], s8[2 * j], s8[2 * j + 1], h[j], l[j]);
+    split_f16x2_neglo_scaled2(x[2 * j], x[2 * j + 1], s8[2 * j], s8[2 * j + 1], h[j], l[j]);
   const uint32_t off = sw128_offset(rows, r, c);
   *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
@@ -160,6 +174,7 @@ __device__ __forceinline__ void issue_stage(uint8_t* base, int nmax, int n, int 
   const int a_mn = (stage == 2 || stage == 4) ? 1 : 0;
   const int b_mn = (stage == 3 || stage == 4) ? 1 : 0;
   const uint32_t idesc = idesc_f16_f32(128, n, a_mn, b_mn);
+  const uint32_t idesc_na = idesc_f16_f32(128, n, a_mn, b_mn, 0, 1);  // A = the negated lo
   const uint32_t a_hi = smem_u32(base + tc_off_op(nmax, f, 0));
   const uint32_t a_lo = smem_u32(base + tc_off_op(nmax, f, 1));
   const uint32_t b_hi = smem_u32(base + tc_off_c(nmax, 0));
@@ -174,7 +189,7 @@ __device__ __forceinline__ void issue_stage(uint8_t* base, int nmax, int n, int 
     const uint64_t bh = sdesc_sw128(b_hi + b_off, b_lbo, 1024u);
     const uint64_t bl = sdesc_sw128(b_lo + b_off, b_lbo, 1024u);
     mma_f16(d_tmem, ah, bl, idesc, kk > 0 ? 1u : 0u);
-    mma_f16(d_tmem, al, bh, idesc, 1u);
+    mma_f16(d_tmem, al, bh, idesc_na, 1u);
   }
   for (int kk = 0; kk < n / 16; ++kk) {  // main products last (see tc_rz_comp)
     const uint32_t a_off = a_mn ? (uint32_t)kk * 2048u : (uint32_t)(kk >> 2) * 16384u + (kk & 3) * 32u;
@@ -207,7 +222,7 @@ __device__ __forceinline__ void tc_pop_group(const DevProblem& pb, const WorkQue
 // reaction / observation pass and the three stage conversions of every step.
 __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl, uint8_t* base,
                              int nmax, int n, uint32_t tmem, int f, int warp, int lane,
-                             uint32_t& ph_done, uint32_t& ph_st, float* fields,
+                             uint32_t& ph_done, float* fields,
                              size_t field_stride) {
   volatile int* abort = &ctl->abort;
   const int l = 32 * (warp & 3) + lane;
@@ -237,12 +252,12 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
   const float kap = tc_rz_comp(n);
   for (int step = 0;; ++step) {
     if (step > 0) {
+      // stage 4 of both fields done: the fourth commit of a step completes an
+      // odd phase of each mma_done, and the other field's stage-4 phase is the
+      // one pending or just completed (the MMAs complete in issue order)
       if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
       ++ph_done;
-      tc_fence_after();
-      mbar_arrive(&ctl->st_ready);
-      if (!mbar_wait_bounded(&ctl->st_ready, ph_st & 1u, abort, pb.wait_ns)) return false;
-      ++ph_st;
+      if (!mbar_wait_bounded(&ctl->mma_done[f ^ 1], 1u, abort, pb.wait_ns)) return false;
       tc_fence_after();
     }
     const bool last = (step == pb.n_steps);
@@ -301,22 +316,25 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
         store_zero8(op_hi[1], op_lo[1], 128, l, x);
         continue;
       }
+      // 256 r (the operand scale, applied through the constants: exact)
       float ru[8], rv[8];
+      const float ftg8 = 256.f * ftg, cu8 = 256.f * cu, cv8 = 256.f * cv;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const float uu = ref_u + du[j], vv = ref_v + dv[j];
         const float u2v = uu * uu * vv;
-        ru[j] = fmaf(ftg, fa - uu + u2v, du[j]) + cu;
-        rv[j] = fmaf(ftg, fb - u2v, dv[j]) + cv;
+        ru[j] = fmaf(ftg8, fa - uu + u2v, fmaf(du[j], 256.f, cu8));
+        rv[j] = fmaf(ftg8, fb - u2v, fmaf(dv[j], 256.f, cv8));
       }
-      store_split8(op_hi[0], op_lo[0], 128, l, x, ru, 256.f);
-      store_split8(op_hi[1], op_lo[1], 128, l, x, rv, 256.f);
+      store_split8n(op_hi[0], op_lo[0], 128, l, x, ru);
+      store_split8n(op_hi[1], op_lo[1], 128, l, x, rv);
     }
     if (obs) ++next_obs;
     if (last) break;
     fence_proxy_async_smem();
     tc_fence_before();
-    mbar_arrive(&ctl->rx_ready);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ctl->rx_ready);
 
     // ---- stage 1 -> MN-major operand of stage 2 (row y, columns p n + k)
     if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
@@ -332,7 +350,8 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     }
     fence_proxy_async_smem();
     tc_fence_before();
-    mbar_arrive(&ctl->op_ready[f]);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ctl->op_ready[f]);
 
     // ---- stage 2 -> scale by L -> K-major operand of stage 3 (row l)
     if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
@@ -370,7 +389,8 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     }
     fence_proxy_async_smem();
     tc_fence_before();
-    mbar_arrive(&ctl->op_ready[f]);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ctl->op_ready[f]);
 
     // ---- stage 3 -> MN-major operand of stage 4 (row k, columns p n + y)
     if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
@@ -386,7 +406,8 @@ __device__ bool tc_converter(const DevProblem& pb, const DevSize& S, TcCtrl* ctl
     }
     fence_proxy_async_smem();
     tc_fence_before();
-    mbar_arrive(&ctl->op_ready[f]);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ctl->op_ready[f]);
   }
   if (valid) {
     atomicAdd(&ctl->phi[p], phi);
@@ -451,10 +472,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0) {
     mbar_init(&ctl->mma_done[0], 1);
     mbar_init(&ctl->mma_done[1], 1);
-    mbar_init(&ctl->op_ready[0], 128);
-    mbar_init(&ctl->op_ready[1], 128);
-    mbar_init(&ctl->rx_ready, 256);
-    mbar_init(&ctl->st_ready, 256);
+    mbar_init(&ctl->op_ready[0], 4);
+    mbar_init(&ctl->op_ready[1], 4);
+    mbar_init(&ctl->rx_ready, 8);
     mbar_init(&ctl->fin, 1);
     mbar_init(&ctl->never, 1);
     ctl->abort = 0;
@@ -465,7 +485,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
 
-  uint32_t ph_done = 0, ph_st = 0, ph_rx = 0;
+  uint32_t ph_done = 0, ph_rx = 0;
   uint32_t ph_op[2] = {0, 0};
   int cur_size = -1;
   for (;;) {
@@ -537,8 +557,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
 
     if (warp < 8) {
-      tc_converter(pb, S, ctl, base, NMAX, n, tmem, warp >> 2, warp, lane, ph_done, ph_st,
-                   fields, field_stride);
+      tc_converter(pb, S, ctl, base, NMAX, n, tmem, warp >> 2, warp, lane, ph_done, fields,
+                   field_stride);
     } else {
       tc_issuer(pb, ctl, base, NMAX, n, tmem, lane, ph_rx, ph_op);
     }

@@ -28,9 +28,17 @@
 // The diagonal factor L = 1 / (alpha + beta (mu_l + mu_k)) (times 1/64 and
 // the compensation below) is computed where it is applied: the reciprocal by
 // the hardware approximation (within one ulp), on pairs of columns with the
-// paired FP32 instructions.  The hi/lo operand split uses
-// the paired instructions too: the converter warps are instruction-bound,
-// and the tensor core waits on them.
+// paired FP32 instructions.  On a fixed domain L is the same every step, so
+// its rounding error compounds in the slow modes: a cheaper reciprocal (one
+// approximation for two values through their product) moved Phi by more
+// than the posterior allows.  The converter warps are bound by their
+// instruction count (twice the warps did not convert faster), and the
+// tensor core waits on them, so the hot loops save instructions: the hi/lo
+// split works on pairs with the paired FP32 instructions and stores the lo
+// part negated (one mixed FP16/FP32 subtraction per value; the MMAs that
+// read it set the negate bit of B), the operand scale 256 of the reaction
+// is applied through its constants, and stage 3's compensation is folded
+// into L.
 //
 // Accumulation order.  The tensor core rounds each MMA's sum toward zero, a
 // bias of about 0.72 * 2^-24 of the accumulator per MMA that compounds over
@@ -44,8 +52,13 @@
 // two FP16 per column) | field u accumulator | field v accumulator.
 // One 128^2 proposal per CTA, 544 threads: warps 0-7 convert field u,
 // 8-15 field v (two warps per TMEM lane quadrant), warp 16 allocates TMEM
-// and issues the MMAs.  Shared memory: the four operand tiles (u hi, u lo,
-// v hi, v lo; 32 KB each) and control.
+// and issues the MMAs, one thread, in the order u1 v1 u2 v2 ... u4 v4 (two
+// issuing threads let both fields' MMAs share the tensor core at once: they
+// then finish together and convert together, with nothing to overlap).  As
+// the MMAs complete in that order, a converter starts the reaction once it
+// has seen the stage-4 commit of both fields.  Barrier arrivals are one per
+// warp.  Shared memory: the four operand tiles (u hi, u lo, v hi, v lo;
+// 32 KB each) and control.
 // Bounded waits as in rd_solve_tc.cu.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -69,25 +82,25 @@ constexpr uint32_t kOffCtrl = 4 * kTileBytes;  // after the tiles u hi, u lo, v 
 constexpr uint32_t kSmemBytes = 1024 + kOffCtrl + 4096;
 // stage output scales with the round-toward-zero compensation 1 + 2^-22
 constexpr float kScale1 = 0x1p-7f + 0x1p-29f;   // stage 1: (1/128)(1 + 2^-22)
-constexpr float kScaleL = 0x1p-6f + 0x1p-28f;   // stage 2: L (1/64)(1 + 2^-22)
-constexpr float kScale3 = 1.f + 0x1p-22f;       // stage 3
+// stage 2: L (1/64)(1 + 2^-22)^2, the compensation of stage 3 included
+// (the transforms are linear), so that stage 3's output is split unscaled
+constexpr float kScaleL = 0x1p-6f + 0x1p-27f;
 constexpr float kScaleW = 0x1p-7f + 0x1p-29f;   // stage 4 (state read): (1/128)(1 + 2^-22)
 
 struct Ctrl {
   uint64_t mma_done[2];   // per field: its stage's MMAs completed
   uint64_t op_all[2];     // per field: the whole next operand written
   uint64_t rx_ready;      // reaction written (both fields)
-  uint64_t st_ready;      // both fields' stage 4 observed
   uint64_t fin;
   uint64_t never;         // completed by nothing (failure-path test aid)
+  double phi;
   uint32_t tmem_base;
   int abort;
   int item;
   int size;
   int bad;
-  double phi;
   double th[kNPhys];
-  float mu[N];
+  alignas(16) float mu[N];
 };
 
 __device__ __forceinline__ uint8_t* tile(uint8_t* base, int f, int hl) {
@@ -107,6 +120,7 @@ __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t bde
 // blocks first, then the main products.
 __device__ __forceinline__ void issue_kmajor(uint8_t* base, uint32_t tmem, int stage, int f) {
   constexpr uint32_t idesc = idesc_f16_f32(128, N, 0, 0);
+  constexpr uint32_t idesc_nb = idesc_f16_f32(128, N, 0, 0, 1);  // B = the negated lo
   const uint32_t a_hi = tmem + (stage <= 2 ? kColCHi : kColCtHi);
   const uint32_t a_lo = tmem + (stage <= 2 ? kColCLo : kColCtLo);
   const uint64_t bh = sdesc_sw128(smem_u32(tile(base, f, 0)), 16u, 1024u);
@@ -115,7 +129,7 @@ __device__ __forceinline__ void issue_kmajor(uint8_t* base, uint32_t tmem, int s
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
     const uint64_t off = ((uint32_t)(kk >> 2) * 16384u + (uint32_t)(kk & 3) * 32u) >> 4;
-    mma_ts(d, a_hi + (uint32_t)(kk * 8), bl + off, idesc, kk > 0 ? 1u : 0u);
+    mma_ts(d, a_hi + (uint32_t)(kk * 8), bl + off, idesc_nb, kk > 0 ? 1u : 0u);
     mma_ts(d, a_lo + (uint32_t)(kk * 8), bh + off, idesc, 1u);
   }
 #pragma unroll
@@ -129,6 +143,7 @@ __device__ __forceinline__ void issue_kmajor(uint8_t* base, uint32_t tmem, int s
 // conversion, two 64-column N blocks 16 KB apart), corrections first.
 __device__ __forceinline__ void issue_stage3(uint8_t* base, uint32_t tmem, int f) {
   constexpr uint32_t idesc = idesc_f16_f32(128, N, 0, 1);
+  constexpr uint32_t idesc_nb = idesc_f16_f32(128, N, 0, 1, 1);  // B = the negated lo
   const uint32_t a_hi = tmem + kColCtHi, a_lo = tmem + kColCtLo;
   const uint64_t bh = sdesc_sw128(smem_u32(tile(base, f, 0)), 16384u, 1024u);
   const uint64_t bl = sdesc_sw128(smem_u32(tile(base, f, 1)), 16384u, 1024u);
@@ -136,7 +151,7 @@ __device__ __forceinline__ void issue_stage3(uint8_t* base, uint32_t tmem, int f
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
     const uint64_t off = ((uint32_t)kk * 2048u) >> 4;
-    mma_ts(d, a_hi + (uint32_t)(kk * 8), bl + off, idesc, kk > 0 ? 1u : 0u);
+    mma_ts(d, a_hi + (uint32_t)(kk * 8), bl + off, idesc_nb, kk > 0 ? 1u : 0u);
     mma_ts(d, a_lo + (uint32_t)(kk * 8), bh + off, idesc, 1u);
   }
 #pragma unroll
@@ -146,13 +161,23 @@ __device__ __forceinline__ void issue_stage3(uint8_t* base, uint32_t tmem, int f
   }
 }
 
-// Splits 8 values (times scale) of row r, columns c..c+7 into the hi and lo
-// tiles: one 16-byte store each.
+// Splits 8 values (times scale) of row r, columns c..c+7 into the hi and
+// negated lo tiles: one 16-byte store each.
 __device__ __forceinline__ void store8(uint8_t* hi, uint8_t* lo, int r, int c, const float* x,
                                        float scale) {
   uint32_t h[4], l[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) split_f16x2_scaled(x[2 * j], x[2 * j + 1], scale, h[j], l[j]);
+  for (int j = 0; j < 4; ++j) split_f16x2_neglo_scaled(x[2 * j], x[2 * j + 1], scale, h[j], l[j]);
+  const uint32_t off = sw128_offset(128, r, c);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// As store8 without a scale.
+__device__ __forceinline__ void store8n(uint8_t* hi, uint8_t* lo, int r, int c, const float* x) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) split_f16x2_neglo(x[2 * j], x[2 * j + 1], h[j], l[j]);
   const uint32_t off = sw128_offset(128, r, c);
   *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
@@ -164,7 +189,7 @@ __device__ __forceinline__ void store8s(uint8_t* hi, uint8_t* lo, int r, int c, 
   uint32_t h[4], l[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j)
-    split_f16x2_scaled2(x[2 * j], x[2 * j + 1], s8[2 * j], s8[2 * j + 1], h[j], l[j]);
+    split_f16x2_neglo_scaled2(x[2 * j], x[2 * j + 1], s8[2 * j], s8[2 * j + 1], h[j], l[j]);
   const uint32_t off = sw128_offset(128, r, c);
   *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
@@ -172,16 +197,17 @@ __device__ __forceinline__ void store8s(uint8_t* hi, uint8_t* lo, int r, int c, 
 
 // Explicit reaction in place on 8 points: state (x 128) ->
 // r_u = du + tau gamma (a - u + u^2 v) (+ cu), r_v = dv + tau gamma (b - u^2 v)
-// (+ cv), as deviations from the reference state.
+// (+ cv), as deviations from the reference state, times 256 (the operand
+// scale, applied through the constants: exact).
 __device__ __forceinline__ void react8(float* u, float* v, float sw, float ref_u, float ref_v,
                                        float fa, float fb, float ftg, float cu, float cv) {
+  const float sw8 = 256.f * sw, ftg8 = 256.f * ftg, cu8 = 256.f * cu, cv8 = 256.f * cv;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const float du = u[j] * sw, dv = v[j] * sw;
-    const float uu = ref_u + du, vv = ref_v + dv;
+    const float uu = fmaf(u[j], sw, ref_u), vv = fmaf(v[j], sw, ref_v);
     const float u2v = uu * uu * vv;
-    u[j] = fmaf(ftg, fa - uu + u2v, du) + cu;
-    v[j] = fmaf(ftg, fb - u2v, dv) + cv;
+    u[j] = fmaf(ftg8, fa - uu + u2v, fmaf(u[j], sw8, cu8));
+    v[j] = fmaf(ftg8, fb - u2v, fmaf(v[j], sw8, cv8));
   }
 }
 
@@ -229,7 +255,7 @@ __device__ __forceinline__ void observe8(const DevProblem& pb, const DevSize& S,
 // xw = 32 / WPF, p = w / 4.
 template <int WPF>
 __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uint8_t* base,
-                          uint32_t tmem, int warp, int lane, uint32_t& ph_done, uint32_t& ph_st,
+                          uint32_t tmem, int warp, int lane, uint32_t& ph_done,
                           float* fields, size_t field_stride) {
   constexpr int CW = 64 / WPF;  // stage-conversion columns per half
   constexpr int XW = 32 / WPF;  // reaction columns per half
@@ -260,13 +286,12 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
   int bad = 0;
   int next_obs = 0;
   for (int step = 0;; ++step) {
-    if (step > 0) {
+    if (step > 0) {  // stage 4 of both fields done: the fourth commit of a step
+      // completes an odd phase, and the other field's stage-4 phase is the one
+      // pending or just completed (the MMAs complete in issue order)
       if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
       ++ph_done;
-      tc_fence_after();
-      mbar_arrive(&ctl->st_ready);
-      if (!mbar_wait_bounded(&ctl->st_ready, ph_st & 1u, abort, pb.wait_ns)) return false;
-      ++ph_st;
+      if (!mbar_wait_bounded(&ctl->mma_done[f ^ 1], 1u, abort, pb.wait_ns)) return false;
       tc_fence_after();
     }
     const bool last = step == pb.n_steps;
@@ -303,14 +328,15 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
         if (o.yo || o.fo) observe8(pb, S, o, l, x0 + j, uh + j, vh + j, sw, phi, bad);
         if (last) continue;
         react8(uh + j, vh + j, sw, ref_u, ref_v, fa, fb, ftg, cu, cv);
-        store8(hi_u, lo_u, l, x0 + j, uh + j, 256.f);
-        store8(hi_v, lo_v, l, x0 + j, vh + j, 256.f);
+        store8n(hi_u, lo_u, l, x0 + j, uh + j);
+        store8n(hi_v, lo_v, l, x0 + j, vh + j);
       }
     }
     if (last) break;
     fence_proxy_async_smem();
     tc_fence_before();
-    mbar_arrive(&ctl->rx_ready);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ctl->rx_ready);
 
     // ---- stages 1-3 of field f -> operands of stages 2-4
 #pragma unroll 1
@@ -318,7 +344,7 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
       if (!mbar_wait_bounded(&ctl->mma_done[f], ph_done & 1u, abort, pb.wait_ns)) return false;
       ++ph_done;
       tc_fence_after();
-      const float sc = stage == 1 ? kScale1 : stage == 3 ? kScale3 : 1.f;
+
       // this warp's 64 columns in 4 chunks of 16, the next chunk's TMEM load in
       // flight while the current one is converted
       constexpr int NQ = CW / 8;  // chunks of 16 columns, both halves
@@ -351,13 +377,19 @@ __device__ bool converter(const DevProblem& pb, const DevSize& S, Ctrl* ctl, uin
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < 16; k += 8) store8(hi_f, lo_f, l, c0 + k, a + k, sc);
+          for (int k = 0; k < 16; k += 8) {
+            if (stage == 1)
+              store8(hi_f, lo_f, l, c0 + k, a + k, kScale1);
+            else
+              store8n(hi_f, lo_f, l, c0 + k, a + k);
+          }
         }
         if (q < NQ - 1) tmem_wait_ld();
       }
       fence_proxy_async_smem();
       tc_fence_before();
-      mbar_arrive(&ctl->op_all[f]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->op_all[f]);
     }
   }
   atomicAdd(&ctl->phi, phi);
@@ -427,10 +459,9 @@ __global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
   if (tid == 0) {
     for (int f = 0; f < 2; ++f) {
       mbar_init(&ctl->mma_done[f], 1);
-      mbar_init(&ctl->op_all[f], 32 * kConvWarps / 2);
+      mbar_init(&ctl->op_all[f], kConvWarps / 2);
     }
-    mbar_init(&ctl->rx_ready, 32 * kConvWarps);
-    mbar_init(&ctl->st_ready, 32 * kConvWarps);
+    mbar_init(&ctl->rx_ready, kConvWarps);
     mbar_init(&ctl->fin, 1);
     mbar_init(&ctl->never, 1);
     ctl->abort = 0;
@@ -469,7 +500,7 @@ __global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
     tmem_wait_st();
   }
   for (int i = tid; i < N; i += kThreads) ctl->mu[i] = S0.mu[i];
-  uint32_t ph_done = 0, ph_st = 0, ph_rx = 0;
+  uint32_t ph_done = 0, ph_rx = 0;
   uint32_t ph_all[2] = {0, 0};
   for (;;) {
     tc_fence_before();
@@ -510,7 +541,7 @@ __global__ void __launch_bounds__(32 * (8 * WPF + 1), 1)
     __syncthreads();
     tc_fence_after();
     if (warp < kConvWarps)
-      converter<WPF>(pb, S, ctl, base, tmem, warp, lane, ph_done, ph_st, fields, field_stride);
+      converter<WPF>(pb, S, ctl, base, tmem, warp, lane, ph_done, fields, field_stride);
     else
       issuer(pb, ctl, base, tmem, lane, ph_rx, ph_all);
     tc_fence_before();

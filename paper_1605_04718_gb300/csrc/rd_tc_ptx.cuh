@@ -173,11 +173,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// Instruction descriptor of kind::f16: D = F32, A = B = F16, A/B K-major (0)
-// or MN-major (1), N >> 3 at bits 17..22, M >> 4 at bits 24..28.
-__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N, int a_mn, int b_mn) {
-  return (1u << 4) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16: D = F32, A = B = F16, A negated
+// (bit 13) if neg_a, B negated (bit 14) if neg_b, A/B K-major (0) or
+// MN-major (1), N >> 3 at bits 17..22, M >> 4 at bits 24..28.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N, int a_mn, int b_mn,
+                                                     int neg_b = 0, int neg_a = 0) {
+  return (1u << 4) | ((uint32_t)neg_a << 13) | ((uint32_t)neg_b << 14) |
+         ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 // Shared-memory matrix descriptor, 128-byte swizzle: start address, leading
@@ -297,6 +300,44 @@ __device__ __forceinline__ void split_f16x2_scaled2(float a, float b, float sa, 
       "cvt.rn.f16x2.f32 %1, r1, r0;\n\t}"
       : "=r"(hi), "=r"(lo)
       : "f"(a), "f"(b), "f"(sa), "f"(sb));
+}
+// As split_f16x2_scaled2, but nlo holds the negated remainders
+// {fp16(hi_a - a sa), fp16(hi_b - b sb)}: each remainder is one
+// mixed-precision subtraction (FP16 minus FP32, rounded to FP32; exact here)
+// instead of a conversion back to FP32 and a subtraction.  Rounding to
+// nearest is symmetric, so nlo is exactly the negated lo of
+// split_f16x2_scaled2; an MMA that reads it sets its negate bit.
+__device__ __forceinline__ void split_f16x2_neglo_scaled2(float a, float b, float sa, float sb,
+                                                          uint32_t& hi, uint32_t& nlo) {
+  asm("{\n\t.reg .b64 x, s;\n\t.reg .f32 x0, x1, r0, r1;\n\t"
+      ".reg .b16 h0, h1;\n\t"
+      "mov.b64 x, {%2, %3};\n\t"
+      "mov.b64 s, {%4, %5};\n\t"
+      "mul.rn.f32x2 x, x, s;\n\t"
+      "mov.b64 {x0, x1}, x;\n\t"
+      "cvt.rn.f16x2.f32 %0, x1, x0;\n\t"
+      "mov.b32 {h0, h1}, %0;\n\t"
+      "sub.rn.f32.f16 r0, h0, x0;\n\t"
+      "sub.rn.f32.f16 r1, h1, x1;\n\t"
+      "cvt.rn.f16x2.f32 %1, r1, r0;\n\t}"
+      : "=r"(hi), "=r"(nlo)
+      : "f"(a), "f"(b), "f"(sa), "f"(sb));
+}
+// split_f16x2_neglo_scaled2 of unscaled values: hi = {fp16(a), fp16(b)},
+// nlo = {fp16(hi_a - a), fp16(hi_b - b)}.
+__device__ __forceinline__ void split_f16x2_neglo(float a, float b, uint32_t& hi, uint32_t& nlo) {
+  asm("{\n\t.reg .f32 r0, r1;\n\t.reg .b16 h0, h1;\n\t"
+      "cvt.rn.f16x2.f32 %0, %3, %2;\n\t"
+      "mov.b32 {h0, h1}, %0;\n\t"
+      "sub.rn.f32.f16 r0, h0, %2;\n\t"
+      "sub.rn.f32.f16 r1, h1, %3;\n\t"
+      "cvt.rn.f16x2.f32 %1, r1, r0;\n\t}"
+      : "=r"(hi), "=r"(nlo)
+      : "f"(a), "f"(b));
+}
+__device__ __forceinline__ void split_f16x2_neglo_scaled(float a, float b, float s, uint32_t& hi,
+                                                         uint32_t& nlo) {
+  split_f16x2_neglo_scaled2(a, b, s, s, hi, nlo);
 }
 __device__ __forceinline__ void split_f16x2_scaled(float a, float b, float s, uint32_t& hi,
                                                    uint32_t& lo) {
