@@ -50,8 +50,8 @@ KERNELS = {"simt": 1, "stacked": 2, "resident": 3}
 # one the capture ran on, else null.
 TRAFFIC = {
     "k_solve2d_tc128<2>": {
-        "sha256": "695a422399116d66718f0923e970440b3fa0922d64d8d21ccd4d998c8e131b35",
-        "bytes": 1040896 + 0,
+        "sha256": "7f779dff9eedd1fb4793b0a8e584f76fb05d7cc158ba86cce1248e7d59ab2c8e",
+        "bytes": 1102336 + 256,
     },
 }
 TRAFFIC_SOURCES = {  # the kernel's own code (its loads and stores)
