@@ -50,7 +50,7 @@ KERNELS = {"simt": 1, "stacked": 2, "resident": 3}
 # one the capture ran on, else null.
 TRAFFIC = {
     "k_solve2d_tc128<2>": {
-        "sha256": "7f779dff9eedd1fb4793b0a8e584f76fb05d7cc158ba86cce1248e7d59ab2c8e",
+        "sha256": "a6fb8214b6386bfa77af795dbeec585ed5d7c2da3421f652fea7b86df8117e2c",
         "bytes": 1102336 + 256,
     },
 }

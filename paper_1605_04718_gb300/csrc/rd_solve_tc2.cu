@@ -31,9 +31,10 @@
 // paired FP32 instructions.  On a fixed domain L is the same every step, so
 // its rounding error compounds in the slow modes: a cheaper reciprocal (one
 // approximation for two values through their product) moved Phi by more
-// than the posterior allows.  The converter warps are bound by their
-// instruction count (twice the warps did not convert faster), and the
-// tensor core waits on them, so the hot loops save instructions: the hi/lo
+// than the posterior allows.  The converter warps are bound by throughput
+// (their instructions, TMEM loads and shared-memory stores beside the MMAs'
+// operand reads: twice the warps did not convert faster), and the tensor
+// core waits on them, so the hot loops save instructions: the hi/lo
 // split works on pairs with the paired FP32 instructions and stores the lo
 // part negated (one mixed FP16/FP32 subtraction per value; the MMAs that
 // read it set the negate bit of B), the operand scale 256 of the reaction
