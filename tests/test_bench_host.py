@@ -7,7 +7,6 @@ import json
 import subprocess
 import sys
 
-
 import bench
 
 
